@@ -1,0 +1,51 @@
+"""Workload parameters and seeded random tensors (NumPy PCG64 generators).
+
+Workloads (shapes and parameters of the paper's runs, restated for the hard-core boson form):
+
+* CONFIG1 -- d = 4 (boson x aux spin-1/2), D = 2, chi = 8, J = V = 1, h = 5, first-order Trotter,
+  dt = 0.02 to t = 1, CTMRG to 1e-10, measured every 0.1.
+* CONFIG2 -- D = 3, chi = 18, J = V = 1, h in {1, 5, 10}, second-order Trotter, dt = 0.05 to t = 5,
+  measured every 0.25.
+* CONFIG3 -- standalone CTMRG contraction on random iPEPS tensors (4, D, D, D, D) with i.i.d.
+  N(0,1) + i N(0,1) entries scaled to unit largest singular value of the 4 x D^4 matricisation;
+  D in {4, 5, 6}, chi = 2 D^2, 20 sweeps.  A uses seed 0, B seed 1.
+"""
+import numpy as np
+
+CONFIG1 = dict(J=1.0, V=1.0, h=5.0, D=2, chi=8, order=1, dt=0.02, t_max=1.0, meas_every=0.1,
+               tol=1e-10)
+CONFIG2 = dict(J=1.0, V=1.0, hs=(1.0, 5.0, 10.0), D=3, chi=18, order=2, dt=0.05, t_max=5.0,
+               meas_every=0.25, tol=1e-10)
+CONFIG3 = dict(Ds=(4, 5, 6), sweeps=20, seeds=(0, 1))
+
+
+def gaussian_complex(shape, seed):
+    """i.i.d. N(0,1) + i N(0,1) entries from numpy.random.default_rng(seed)."""
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+def config3_tensors(D, d=4, seeds=(0, 1)):
+    """Random site tensors A, B of shape (d, D, D, D, D), each with unit largest singular value
+    of its d x D^4 matricisation."""
+    out = []
+    for seed in seeds:
+        t = gaussian_complex((d, D, D, D, D), seed)
+        t = t / np.linalg.norm(t.reshape(d, -1), 2)
+        out.append(t.astype(np.complex128))
+    return out[0], out[1]
+
+
+def random_site_tensors(d, D, seed, product_weight=1.0, noise=0.3):
+    """Short-correlated random site tensors: a product-state part on bond index 0 plus seeded noise.
+
+    Returns A, B of shape (d, D, D, D, D).  Used to build small test networks whose correlation
+    length is short enough for finite tori to approach the infinite lattice quickly."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(2):
+        t = noise * (rng.standard_normal((d, D, D, D, D)) + 1j * rng.standard_normal((d, D, D, D, D)))
+        v = rng.standard_normal(d) + 1j * rng.standard_normal(d)
+        t[:, 0, 0, 0, 0] += product_weight * v / np.linalg.norm(v)
+        out.append(t)
+    return out[0], out[1]

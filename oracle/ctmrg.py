@@ -1,0 +1,287 @@
+"""Directional CTMRG with full 2x2-block projectors, explicit double layer (FP64, plain NumPy).
+
+TEST INFRASTRUCTURE ONLY -- see ``oracle/__init__.py``.
+
+Paper: Sec. "Set up for iPEPS" (Readout) and the Appendix use CTMRG (Orus & Vidal, PRB 80, 094403
+(2009); Orus, PRB 85, 205117 (2012); Nishino & Okunishi 1996/97) to contract the infinite lattice
+around a site into fixed-point corner and edge tensors, with environment dimension chi >= D^2,
+"sufficiently well converged".  The projectors follow Corboz, Rice & Troyer, PRL 113, 046402 (2014):
+from the four enlarged corners Q1..Q4 of a 2x2 block, R = Q3 Q4 (lower half) and R~ = Q1 Q2 (upper
+half) are contracted over the bond to be truncated, M = R R~ = U S V^+, and
+
+    P = R~ V S^{-1/2}   (attached to the lower side of the cut)
+    P~ = S^{-1/2} U^+ R (attached to the upper side of the cut)
+
+so that P~ P = 1 and R P P~ R~ is the best rank-chi approximation of M.
+
+Unit cell Lx x Ly (here 2 x 2 with A on x+y even, B on x+y odd).  Coordinates: x grows to the
+right, y grows downwards.
+
+Tensor conventions (every environment index order follows the clockwise walk around the site
+C1 -> T1 -> C2 -> T2 -> C3 -> T3 -> C4 -> T4 -> C1; the last index of each tensor joins the first
+index of the next; chi indices first/last, the D^2 index in the middle):
+
+    C1[c_T4, c_T1]      T1[left, k_U, right]
+    C2[c_T1, c_T2]      T2[up,   k_R, down]
+    C3[c_T2, c_T3]      T3[right, k_D, left]
+    C4[c_T3, c_T4]      T4[down, k_L, up]
+
+    double layer a[U, L, D, R], each index (ket, bra) -> ket * D + bra, dimension D^2.
+
+A 90-degree counter-clockwise rotation of the lattice maps site (x, y) to (y, -x), the site tensor
+to a.transpose(3, 0, 1, 2), and the environment (C1..C4, T1..T4) to (C2, C3, C4, C1; T2, T3, T4, T1)
+with no index permutation -- so one left move plus rotations gives all four directional moves.
+
+Degenerate singular values at the cut are kept or dropped as whole multiplets; singular values
+below PROJ_CUT_REL of the largest are dropped (pseudo-inverse); the kept rank is zero-padded to chi.
+
+Parity: pinned by tests/test_oracle_ctmrg.py (Ising PEPS against Onsager/Yang, exact dimer states,
+brute-force contraction of small periodic tori, product states at chi = 1, rotation invariance).
+"""
+import functools
+
+import numpy as np
+
+from .su import truncation_rank
+
+# every contraction below is a pairwise (or three-operand) einsum; optimize=True lets NumPy hand
+# each pairwise step to BLAS and changes nothing but speed
+ein = functools.partial(np.einsum, optimize=True)
+
+PROJ_CUT_REL = 1e-10
+
+
+# ----------------------------------------------------------------------------- double layer
+def double_layer(A):
+    """a[(u u'), (l l'), (d d'), (r r')] = sum_s A[s,u,l,d,r] conj(A[s,u',l',d',r'])."""
+    D = A.shape[1]
+    a = ein('suldr,svmew->uvlmderw', A, A.conj())
+    return a.reshape(D * D, D * D, D * D, D * D)
+
+
+def double_layer_open(A):
+    """Open double layer ao[s, s', U, L, D, R] (physical ket/bra indices kept)."""
+    D = A.shape[1]
+    ao = ein('suldr,tvmew->stuvlmderw', A, A.conj())
+    return ao.reshape(A.shape[0], A.shape[0], D * D, D * D, D * D, D * D)
+
+
+def _trace_pair(a, D, axes):
+    """Trace the ket/bra pair of each leg in ``axes`` of a double-layer tensor; keep the rest."""
+    t = a.reshape([D, D] * 4)
+    letters = 'abcdefgh'
+    spec_in = ''
+    spec_out = ''
+    for leg in range(4):
+        k, b = letters[2 * leg], letters[2 * leg + 1]
+        if leg in axes:
+            spec_in += k + k
+        else:
+            spec_in += k + b
+            spec_out += k + b
+    out = ein(spec_in + '->' + spec_out, t)
+    return out.reshape([D * D] * (4 - len(axes)))
+
+
+# ----------------------------------------------------------------------------- environment
+class Env:
+    """Corner and edge tensors per unit-cell site: C[i][(x, y)], T[i][(x, y)], i = 0..3 (C1..C4)."""
+
+    def __init__(self, Lx, Ly, C, T):
+        self.Lx, self.Ly = Lx, Ly
+        self.C, self.T = C, T
+
+    def copy(self):
+        return Env(self.Lx, self.Ly, [dict((k, v.copy()) for k, v in c.items()) for c in self.C],
+                   [dict((k, v.copy()) for k, v in t.items()) for t in self.T])
+
+
+def _pad(t, shape):
+    out = np.zeros(shape, dtype=np.complex128)
+    out[tuple(slice(0, n) for n in t.shape)] = t
+    return out
+
+
+def init_env(a, Lx, Ly, chi, D):
+    """Initial environment: each outward ket/bra leg pair of the neighbouring double layer traced,
+    giving chi_init = D^2, zero-padded to chi.  a[(x, y)] are the double layers."""
+    if chi < D * D:
+        raise ValueError("chi must be >= D^2")
+    D2 = D * D
+    C = [{}, {}, {}, {}]
+    T = [{}, {}, {}, {}]
+    for x in range(Lx):
+        for y in range(Ly):
+            def at(dx, dy):
+                return a[((x + dx) % Lx, (y + dy) % Ly)]
+            # corners: keep the two inner legs, ordered clockwise
+            C[0][(x, y)] = _pad(_trace_pair(at(-1, -1), D, (0, 1)), (chi, chi))   # [D, R]
+            c2 = _trace_pair(at(1, -1), D, (0, 3))                                # [L, D]
+            C[1][(x, y)] = _pad(c2, (chi, chi))
+            c3 = _trace_pair(at(1, 1), D, (2, 3))                                 # [U, L]
+            C[2][(x, y)] = _pad(c3, (chi, chi))
+            c4 = _trace_pair(at(-1, 1), D, (1, 2))                                # [U, R]
+            C[3][(x, y)] = _pad(c4.T, (chi, chi))                                 # [R, U]
+            # edges
+            t1 = _trace_pair(at(0, -1), D, (0,))                                  # [L, D, R]
+            T[0][(x, y)] = _pad(t1, (chi, D2, chi))
+            t2 = _trace_pair(at(1, 0), D, (3,))                                   # [U, L, D]
+            T[1][(x, y)] = _pad(t2, (chi, D2, chi))
+            t3 = _trace_pair(at(0, 1), D, (2,))                                   # [U, L, R]
+            T[2][(x, y)] = _pad(np.transpose(t3, (2, 0, 1)), (chi, D2, chi))      # [R, U, L]
+            t4 = _trace_pair(at(-1, 0), D, (1,))                                  # [U, D, R]
+            T[3][(x, y)] = _pad(np.transpose(t4, (1, 2, 0)), (chi, D2, chi))      # [D, R, U]
+    return Env(Lx, Ly, C, T)
+
+
+def rotate(a, env):
+    """Rotate the whole network by 90 degrees counter-clockwise: (x, y) -> (y, -x)."""
+    Lx, Ly = env.Lx, env.Ly
+
+    def np_(p):
+        return (p[1] % Ly, (-p[0]) % Lx)
+
+    a2 = {np_(p): np.transpose(t, (3, 0, 1, 2)) for p, t in a.items()}
+    C2 = [{np_(p): t for p, t in env.C[(i + 1) % 4].items()} for i in range(4)]
+    T2 = [{np_(p): t for p, t in env.T[(i + 1) % 4].items()} for i in range(4)]
+    return a2, Env(Ly, Lx, C2, T2)
+
+
+# ----------------------------------------------------------------------------- enlarged corners
+def corner_q1(C1, T1, T4, a):
+    """Q1[(e4, kD), (e1, kR)] = C1[c4,c1] T1[c1,kU,e1] T4[e4,kL,c4] a[kU,kL,kD,kR]."""
+    x = ein('pc,cue->pue', C1, T1)
+    x = ein('flp,pue->fleu', T4, x)
+    x = ein('fleu,ulkr->fker', x, a)
+    chi, D2 = C1.shape[0], a.shape[0]
+    return x.reshape(chi * D2, chi * D2)
+
+
+def corner_q2(T1, C2, T2, a):
+    """Q2[(e1, kL), (e2, kD)] = T1[e1,kU,c1] C2[c1,c2] T2[c2,kR,e2] a[kU,kL,kD,kR]."""
+    x = ein('euc,cp->eup', T1, C2)
+    x = ein('eup,prf->eurf', x, T2)
+    x = ein('eurf,ulkr->elfk', x, a)
+    chi, D2 = C2.shape[0], a.shape[0]
+    return x.reshape(chi * D2, chi * D2)
+
+
+def corner_q3(T2, C3, T3, a):
+    """Q3[(e2, kU), (e3, kL)] = T2[e2,kR,c2] C3[c2,c3] T3[c3,kD,e3] a[kU,kL,kD,kR]."""
+    x = ein('erc,cp->erp', T2, C3)
+    x = ein('erp,pkf->erkf', x, T3)
+    x = ein('erkf,ulkr->eufl', x, a)
+    chi, D2 = C3.shape[0], a.shape[0]
+    return x.reshape(chi * D2, chi * D2)
+
+
+def corner_q4(T3, C4, T4, a):
+    """Q4[(e3, kR), (e4, kU)] = T3[e3,kD,c3] C4[c3,c4] T4[c4,kL,e4] a[kU,kL,kD,kR]."""
+    x = ein('ekc,cp->ekp', T3, C4)
+    x = ein('ekp,plf->eklf', x, T4)
+    x = ein('eklf,ulkr->erfu', x, a)
+    chi, D2 = C4.shape[0], a.shape[0]
+    return x.reshape(chi * D2, chi * D2)
+
+
+# ----------------------------------------------------------------------------- projectors
+def projectors(R, Rt, chi, cut_rel=PROJ_CUT_REL):
+    """Full-SVD projectors for the bond joining R (columns) and R~ (rows); returns (P, P~, s).
+
+    s is the full singular spectrum of M = R R~ (for diagnostics)."""
+    M = R @ Rt
+    U, s, Vh = np.linalg.svd(M)
+    K = truncation_rank(s, chi)
+    K = min(K, int(np.sum(s > cut_rel * s[0]))) if s[0] > 0 else 0
+    K = max(K, 1) if s[0] > 0 else 0
+    N = R.shape[1]
+    P = np.zeros((N, chi), dtype=np.complex128)
+    Pt = np.zeros((chi, N), dtype=np.complex128)
+    if K > 0:
+        isq = 1.0 / np.sqrt(s[:K])
+        P[:, :K] = (Rt @ Vh[:K].conj().T) * isq[None, :]
+        Pt[:K] = (U[:, :K].conj().T @ R) * isq[:, None]
+    return P, Pt, s
+
+
+def _normalize(t):
+    m = np.max(np.abs(t))
+    return t / m if m > 0 else t
+
+
+def left_move(a, env, x, chi):
+    """Absorb column x into the left environment of column x+1 (all rows)."""
+    Lx, Ly = env.Lx, env.Ly
+    C, T = env.C, env.T
+    xp = (x + 1) % Lx
+    D2 = a[(0, 0)].shape[0]
+    P, Pt = {}, {}
+    for y in range(Ly):
+        yp = (y + 1) % Ly
+        q1 = corner_q1(C[0][(x, y)], T[0][(x, y)], T[3][(x, y)], a[(x, y)])
+        q2 = corner_q2(T[0][(xp, y)], C[1][(xp, y)], T[1][(xp, y)], a[(xp, y)])
+        q3 = corner_q3(T[1][(xp, yp)], C[2][(xp, yp)], T[2][(xp, yp)], a[(xp, yp)])
+        q4 = corner_q4(T[2][(x, yp)], C[3][(x, yp)], T[3][(x, yp)], a[(x, yp)])
+        R = q3 @ q4       # rows: bond Q2|Q3, columns: the cut (bond Q4|Q1)
+        Rt = q1 @ q2      # rows: the cut, columns: bond Q2|Q3
+        P[y], Pt[y], _ = projectors(R, Rt, chi)
+    newC1, newT4, newC4 = {}, {}, {}
+    for y in range(Ly):
+        ym = (y - 1) % Ly
+        c1t1 = ein('pc,cue->pue', C[0][(x, y)], T[0][(x, y)]).reshape(chi * D2, chi)
+        newC1[y] = Pt[ym] @ c1t1
+        t4a = ein('flp,ulkr->fkrpu', T[3][(x, y)], a[(x, y)]).reshape(chi * D2, D2, chi * D2)
+        newT4[y] = ein('cm,mkn,nf->ckf', Pt[y], t4a, P[ym])
+        t3c4 = ein('ekc,cp->epk', T[2][(x, y)], C[3][(x, y)]).reshape(chi, chi * D2)
+        newC4[y] = t3c4 @ P[y]
+    for y in range(Ly):
+        C[0][(xp, y)] = _normalize(newC1[y])
+        T[3][(xp, y)] = _normalize(newT4[y])
+        C[3][(xp, y)] = _normalize(newC4[y])
+
+
+def sweep(a, env, chi):
+    """One CTMRG sweep: left, top, right and bottom moves, each over every column."""
+    for _ in range(4):
+        for x in range(env.Lx):
+            left_move(a, env, x, chi)
+        a, env = rotate(a, env)
+    return env
+
+
+def corner_spectra(env, chi):
+    """Normalised singular values of every corner, zero-padded to chi: dict (i, x, y) -> array."""
+    out = {}
+    for i in range(4):
+        for p, c in env.C[i].items():
+            s = np.linalg.svd(c, compute_uv=False)
+            v = np.zeros(chi)
+            if s[0] > 0:
+                v[:len(s)] = s / s[0]
+            out[(i, p)] = v
+    return out
+
+
+def spectra_delta(s_new, s_old):
+    """Convergence number: max over corners of the 2-norm change of the normalised spectrum."""
+    return max(np.linalg.norm(s_new[k] - s_old[k]) for k in s_new)
+
+
+def ctmrg(a, env, chi, tol=1e-10, max_sweeps=200, min_sweeps=1):
+    """Sweep until the corner spectra change by less than ``tol``; returns (env, sweeps, delta)."""
+    prev = corner_spectra(env, chi)
+    delta = np.inf
+    n = 0
+    for n in range(1, max_sweeps + 1):
+        env = sweep(a, env, chi)
+        cur = corner_spectra(env, chi)
+        delta = spectra_delta(cur, prev)
+        prev = cur
+        if n >= min_sweeps and delta < tol:
+            break
+    return env, n, delta
+
+
+def checkerboard(A, B):
+    """Site tensors of the 2x2 unit cell: A on x + y even, B on x + y odd."""
+    return {(x, y): (A if (x + y) % 2 == 0 else B) for x in range(2) for y in range(2)}

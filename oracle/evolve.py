@@ -1,0 +1,71 @@
+"""Time-evolution driver: Trotter steps interleaved with CTMRG convergence and measurement.
+
+TEST INFRASTRUCTURE ONLY -- see ``oracle/__init__.py``.
+
+Paper: Sec. "Set up for iPEPS" -- initialise |Psi_0> (CDW x |+>), quench with the simple update,
+read out local expectation values with CTMRG.  The environment at each measurement time starts from
+the previous measurement's converged environment (warm start); the first one starts from the traced
+double layer (see ``ctmrg.init_env``).
+
+Parity: pinned end to end by tests/test_oracle_evolve.py.
+"""
+import numpy as np
+
+from . import ctmrg, measure, model, su
+
+
+def ctm_state(GA, GB, lam):
+    """Double layers of the 2x2 unit cell and the physical tensors (sqrt(lam) on every leg)."""
+    A, B = su.physical_tensors(GA, GB, lam)
+    a = ctmrg.checkerboard(ctmrg.double_layer(A), ctmrg.double_layer(B))
+    return A, B, a
+
+
+def converge_and_measure(GA, GB, lam, env, p, tol, max_sweeps):
+    A, B, a = ctm_state(GA, GB, lam)
+    if env is None:
+        env = ctmrg.init_env(a, 2, 2, p['chi'], p['D'])
+    env, sweeps, delta = ctmrg.ctmrg(a, env, p['chi'], tol=tol, max_sweeps=max_sweeps)
+    obs = measure.observables(A, B, env, p['J'], p['V'], p['h'], p.get('d_A', 2))
+    obs.update(ctm_sweeps=sweeps, ctm_delta=delta)
+    return env, obs
+
+
+def run(p, tol=1e-10, max_sweeps=500, callback=None):
+    """Evolve with parameters p (J, V, h, D, chi, order, dt, t_max, meas_every[, d_A]).
+
+    Returns a list of observation dicts at t = 0, meas_every, 2 meas_every, ... t_max.
+    """
+    d_A = p.get('d_A', 2)
+    GA, GB, lam = model.initial_tensors(p['D'], d_A)
+    seq = su.trotter_sequence(p['order'], p['dt'])
+    gates = {delta: model.gate(p['J'], p['V'], p['h'], delta, d_A) for _, delta in seq}
+    n_steps = int(round(p['t_max'] / p['dt']))
+    stride = int(round(p['meas_every'] / p['dt']))
+    env = None
+    eps_acc = 0.0
+    out = []
+    for step in range(n_steps + 1):
+        if step % stride == 0:
+            env, obs = converge_and_measure(GA, GB, lam, env, p, tol, max_sweeps)
+            obs.update(t=step * p['dt'], trunc_err_acc=eps_acc, lam=lam.copy())
+            out.append(obs)
+            if callback is not None:
+                callback(obs)
+        if step < n_steps:
+            GA, GB, lam, e = su.trotter_step(GA, GB, lam, gates, p['order'], p['dt'])
+            eps_acc += e
+    return out
+
+
+def evolve_tensors(p, n_steps):
+    """Only the simple-update part: returns (GA, GB, lam, eps_acc) after n_steps Trotter steps."""
+    d_A = p.get('d_A', 2)
+    GA, GB, lam = model.initial_tensors(p['D'], d_A)
+    seq = su.trotter_sequence(p['order'], p['dt'])
+    gates = {delta: model.gate(p['J'], p['V'], p['h'], delta, d_A) for _, delta in seq}
+    eps = 0.0
+    for _ in range(n_steps):
+        GA, GB, lam, e = su.trotter_step(GA, GB, lam, gates, p['order'], p['dt'])
+        eps += e
+    return GA, GB, lam, eps
