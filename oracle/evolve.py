@@ -25,14 +25,15 @@ def converge_and_measure(GA, GB, lam, env, p, tol, max_sweeps):
     A, B, a = ctm_state(GA, GB, lam)
     if env is None:
         env = ctmrg.init_env(a, 2, 2, p['chi'], p['D'])
-    env, sweeps, delta = ctmrg.ctmrg(a, env, p['chi'], tol=tol, max_sweeps=max_sweeps)
+    env, sweeps, delta = ctmrg.ctmrg(a, env, p['chi'], tol=tol, max_sweeps=max_sweeps,
+                                     cut_rel=p.get('cut_rel', ctmrg.PROJ_CUT_REL))
     obs = measure.observables(A, B, env, p['J'], p['V'], p['h'], p.get('d_A', 2))
     obs.update(ctm_sweeps=sweeps, ctm_delta=delta)
     return env, obs
 
 
 def run(p, tol=1e-10, max_sweeps=500, callback=None):
-    """Evolve with parameters p (J, V, h, D, chi, order, dt, t_max, meas_every[, d_A]).
+    """Evolve with parameters p (J, V, h, D, chi, order, dt, t_max, meas_every[, d_A, cut_rel]).
 
     Returns a list of observation dicts at t = 0, meas_every, 2 meas_every, ... t_max.
     """

@@ -1,4 +1,5 @@
-"""Pins for oracle/ctmrg.py and oracle/measure.py.
+"""Pins for oracle/ctmrg.py and oracle/measure.py (engine checks use a projector cutoff of 1e-10
+so that the truncation bias stays below the closed-form tolerances).
 
 * Ising PEPS (norm network = 2D Ising partition function): one-site <sigma^z> equals Yang's
   spontaneous magnetisation, nearest-neighbour <sigma^z sigma^z> equals Onsager's -u/2 on both
@@ -20,12 +21,12 @@ from tests.pins import ising, torus
 SZ = np.diag([1.0, -1.0]).astype(complex)
 
 
-def _converge(A, B, chi, D, tol=1e-10, init_from=None, max_sweeps=300):
+def _converge(A, B, chi, D, tol=1e-10, init_from=None, max_sweeps=300, cut_rel=1e-10):
     a = ctmrg.checkerboard(ctmrg.double_layer(A), ctmrg.double_layer(B))
     a0 = a if init_from is None else ctmrg.checkerboard(ctmrg.double_layer(init_from[0]),
                                                          ctmrg.double_layer(init_from[1]))
     env = ctmrg.init_env(a0, 2, 2, chi, D)
-    env, n, delta = ctmrg.ctmrg(a, env, chi, tol=tol, max_sweeps=max_sweeps)
+    env, n, delta = ctmrg.ctmrg(a, env, chi, tol=tol, max_sweeps=max_sweeps, cut_rel=cut_rel)
     return env, n, delta
 
 
