@@ -1,0 +1,43 @@
+/* Building-block entry points of libipeps (FP64 dense kernels), exported for unit tests.
+ *
+ * These are the kernels the CTMRG / simple-update pipeline is built from; they are not steps of
+ * the paper's method on their own (the paper fixes no kernels).  All pointers are DEVICE pointers
+ * owned by the caller; complex numbers are interleaved (re, im) doubles; matrices are row-major.
+ * Calls are asynchronous on `stream` (a cudaStream_t, NULL = legacy default stream).
+ * Return value: 0 on success, a nonzero ipeps_status code otherwise (see ipeps.h); the text of the
+ * last error on the calling thread is available from ipeps_last_error(NULL).
+ */
+#ifndef IPEPS_KERNELS_H
+#define IPEPS_KERNELS_H
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* C[b] = op(A[b]) * op(B[b]) for b < batch, strided by sA/sB/sC elements.
+ * op: 0 = as stored, 1 = transpose, 2 = conjugate transpose.  op(A) is M x K, op(B) is K x N.
+ * FP64 complex, one 16x16 output tile per CTA. */
+int ipeps_kernel_zgemm(int M, int N, int K, int batch, int opA, int opB,
+                       const double* A, long long lda, long long sA,
+                       const double* B, long long ldb, long long sB,
+                       double* C, long long ldc, long long sC, void* stream);
+
+/* Trotter gate exp(-i h_b delta) of the d = 4 dilated model (J, V, h as in ipeps_params),
+ * computed on the device and copied to the HOST buffer out (16 x 16 complex, row index sA*4+sB).
+ * Allocates and frees a small device buffer; synchronising. */
+int ipeps_kernel_gate(double J, double V, double h, double delta, double* out);
+
+/* out = in permuted: out axis j is in axis perm[j] (rank <= 8, dims[] of the input). */
+int ipeps_kernel_permute(const double* in, double* out, int rank, const int* dims,
+                         const int* perm, int batch, long long s_in, long long s_out, void* stream);
+
+/* Thin SVD A[b] = U[b] diag(S[b]) V[b]^+ of `batch` m x n complex matrices (m >= n), one-sided
+ * Jacobi on a thread-block cluster of 8 CTAs.  U: m x n, S: n (descending), V: n x n, all
+ * contiguous per problem (strides m*n, n, n*n).  U or V may be NULL.  sweeps_out: int[batch] or
+ * NULL.  Returns IPEPS_ENOCONV if a problem hit max_sweeps, IPEPS_ENAN on non-finite input. */
+int ipeps_kernel_svd(int m, int n, int batch, const double* A, double* U, double* S, double* V,
+                     double tol, int max_sweeps, int* sweeps_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,8 @@
+"""GB300-native iPEPS real-time evolution of 2D many-body-localised lattices (arXiv:1910.11359).
+
+The compute path is libipeps.so (hand-written CUDA for sm_103a behind a C ABI, include/ipeps.h);
+this package only loads it and marshals arguments.
+"""
+from ._lib import FP64, SPLIT_BF16X3, SPLIT_TF32X3, IPEPS, IpepsError, footprint_bytes, lib
+
+__all__ = ["FP64", "SPLIT_BF16X3", "SPLIT_TF32X3", "IPEPS", "IpepsError", "footprint_bytes", "lib"]

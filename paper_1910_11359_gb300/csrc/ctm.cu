@@ -1,0 +1,487 @@
+// Directional CTMRG with full 2x2-block projectors on the device (paper Sec. "Set up for iPEPS",
+// Readout, and Appendix: CTMRG of Orus & Vidal 2009 / Orus 2012, chi >= D^2, converged environment;
+// projectors of Corboz, Rice & Troyer, PRL 113, 046402 (2014)).
+//
+// Conventions (shared with the rest of the library):
+//   double layer a[U, L, D, R], each index ket * D + bra (dimension D2 = D^2), rotations
+//   rot^k(a)[i0..i3] = a[i_k .. i_{k+3}] (90-degree counter-clockwise relabellings);
+//   corners C1[c_T4, c_T1], C2[c_T1, c_T2], C3[c_T2, c_T3], C4[c_T3, c_T4];
+//   edges T1[left, k, right], T2[up, k, down], T3[right, k, left], T4[down, k, up]
+//   (clockwise walk: the last index of each tensor joins the first index of the next).
+// A counter-clockwise rotation of the lattice maps (x, y) -> (y, -x), C_i -> C_{i-1}, T_i -> T_{i-1}
+// with no index permutation, so every directional move is the left move in a rotated frame f:
+// logical tensor X_i at logical position q is physical X_{(i + f) mod 4} at position rot^{-f}(q), and
+// the logical site tensor there is rot^f of the physical one.  On the 2 x 2 cell rot^{-f} swaps x
+// and y for odd f.
+//
+// Left move at logical column x, for both cuts y (between rows y and y+1) at once:
+//   enlarged corners Q_i (i = 0..3: the block's top-left, top-right, bottom-right, bottom-left):
+//     Q_i[(e_ccw, k_row), (e_cw, k_col)] = T_ccw[e_ccw, kA, c] C[c, c'] T_cw[c', kB, e_cw]
+//                                          rot^i(a)[kB, kA, k_row, k_col]
+//   R~ = Q_0 Q_1, R = Q_2 Q_3, M = R R~ = U S V^+ (contracted over the cut), truncated to chi:
+//     P = R~ V S^{-1/2} (lower side of the cut), P~ = S^{-1/2} U^+ R (upper side)
+//   C1'(x+1, y) = P~[y-1] (C1 T1),  T4'(x+1, y) = P~[y] (T4 a) P[y-1],  C4'(x+1, y) = (T3 C4) P[y],
+//   each divided by its largest modulus.
+#include <cmath>
+#include <vector>
+
+#include "ctx.cuh"
+#include "model.cuh"
+
+namespace ipeps {
+
+static inline int rot_pos(int pos, int f) {   // physical position of logical position `pos` in frame f
+  return (f & 1) ? pos_of(pos >> 1, pos & 1) : pos;
+}
+
+void ctm_carve(Ctx& c) {
+  Arena& a = c.arena;
+  const int B = c.B;
+  const long long N2 = c.N2(), Nc = (long long)c.N * c.chi, chi2 = (long long)c.chi * c.chi;
+  const long long T = (long long)c.chi * c.D2 * c.chi;
+  c.Aph = a.take<cplx>((size_t)B * c.d * c.D2 * c.D2);
+  c.Bph = a.take<cplx>((size_t)B * c.d * c.D2 * c.D2);
+  c.arot = a.take<cplx>((size_t)2 * 4 * B * c.D8());
+  for (int i = 0; i < 4; ++i)
+    for (int p = 0; p < NPOS; ++p) {
+      c.Cenv[i][p] = a.take<cplx>((size_t)B * chi2);
+      c.Tenv[i][p] = a.take<cplx>((size_t)B * T);
+    }
+  CtmWork& w = c.w;
+  w.X1 = a.take<cplx>((size_t)8 * B * Nc);
+  w.X2 = a.take<cplx>((size_t)8 * B * N2);
+  w.X2p = a.take<cplx>((size_t)8 * B * N2);
+  w.Y = a.take<cplx>((size_t)8 * B * N2);
+  w.Q = a.take<cplx>((size_t)8 * B * N2);
+  w.H = a.take<cplx>((size_t)4 * B * N2);
+  w.M = a.take<cplx>((size_t)2 * B * N2);
+  w.U = a.take<cplx>((size_t)2 * B * N2);
+  w.V = a.take<cplx>((size_t)2 * B * N2);
+  w.S = a.take<double>((size_t)2 * B * c.N);
+  w.Us = a.take<cplx>((size_t)2 * B * Nc);
+  w.Vs = a.take<cplx>((size_t)2 * B * Nc);
+  w.P = a.take<cplx>((size_t)2 * B * Nc);
+  w.Pt = a.take<cplx>((size_t)2 * B * Nc);
+  w.Z1 = a.take<cplx>((size_t)2 * B * N2);
+  w.Z1p = a.take<cplx>((size_t)2 * B * N2);
+  w.Z2 = a.take<cplx>((size_t)2 * B * N2);
+  w.Z2p = a.take<cplx>((size_t)2 * B * N2);
+  w.T4n = a.take<cplx>((size_t)2 * B * T);
+  w.W1 = a.take<cplx>((size_t)2 * B * T);
+  w.W1p = a.take<cplx>((size_t)2 * B * T);
+  w.C1n = a.take<cplx>((size_t)2 * B * chi2);
+  w.C4n = a.take<cplx>((size_t)2 * B * chi2);
+  w.kept = a.take<int>((size_t)2 * B);
+  w.cs = a.take<double>((size_t)16 * B * c.chi);
+  w.prev = a.take<double>((size_t)16 * B * c.chi);
+  w.delta = a.take<double>(B);
+  w.frozen = a.take<int>(B);
+  w.sweeps = a.take<int>(B);
+  w.have_prev = a.take<int>(1);
+}
+
+void ctm_build_plans(Ctx& c) {
+  const int B = c.B, chi = c.chi, D2 = c.D2;
+  const long long N2 = c.N2(), Nc = (long long)c.N * chi, chi2 = (long long)chi * chi;
+  const long long T = (long long)chi * D2 * chi;
+  PtrPool& pool = c.pool;
+  CtmWork& w = c.w;
+  auto Cp = [&](int i, int pos, int b) -> const void* { return c.Cenv[i & 3][pos] + (size_t)b * chi2; };
+  auto Tp = [&](int i, int pos, int b) -> const void* { return c.Tenv[i & 3][pos] + (size_t)b * T; };
+  for (int f = 0; f < 4; ++f)
+    for (int x = 0; x < 2; ++x) {
+      MoveOff& o = c.off.mv[f][x];
+      std::vector<const void*> g1A, g1B, g1C, g2A, g2B, g2C, g3B;
+      for (int y = 0; y < 2; ++y)
+        for (int i = 0; i < 4; ++i)
+          for (int b = 0; b < B; ++b) {
+            const int lx[4] = {x, x + 1, x + 1, x}, ly[4] = {y, y, y + 1, y + 1};
+            const int pp = rot_pos(pos_of(lx[i], ly[i]), f);
+            const int slot = (y * 4 + i) * B + b;
+            g1A.push_back(Cp(i + f, pp, b));
+            g1B.push_back(Tp(i + f, pp, b));
+            g1C.push_back(w.X1 + (size_t)slot * Nc);
+            g2A.push_back(Tp(i + 3 + f, pp, b));
+            g2B.push_back(w.X1 + (size_t)slot * Nc);
+            g2C.push_back(w.X2 + (size_t)slot * N2);
+            g3B.push_back(c.a_rot(site_of(pp), (i + f) & 3) + (size_t)b * c.D8());
+          }
+      o.g1A = pool.add(g1A); o.g1B = pool.add(g1B); o.g1C = pool.add(g1C);
+      o.g2A = pool.add(g2A); o.g2B = pool.add(g2B); o.g2C = pool.add(g2C);
+      o.g3B = pool.add(g3B);
+      std::vector<const void*> hA, hB, hC;
+      for (int half = 0; half < 2; ++half)          // 0: R~ = Q0 Q1, 1: R = Q2 Q3
+        for (int y = 0; y < 2; ++y)
+          for (int b = 0; b < B; ++b) {
+            const int s0 = (y * 4 + 2 * half) * B + b, s1 = (y * 4 + 2 * half + 1) * B + b;
+            hA.push_back(w.Q + (size_t)s0 * N2);
+            hB.push_back(w.Q + (size_t)s1 * N2);
+            hC.push_back(w.H + (size_t)((half * 2 + y) * B + b) * N2);
+          }
+      o.hA = pool.add(hA); o.hB = pool.add(hB); o.hC = pool.add(hC);
+      std::vector<const void*> c1A, c1B, z1A, z1B, z2B, t4A, w1A, w1B, c4B, sC1, sT4, sC4;
+      for (int y = 0; y < 2; ++y)
+        for (int b = 0; b < B; ++b) {
+          const int ym = (y + 1) & 1;   // y - 1 on the two-row cell
+          const int pp = rot_pos(pos_of(x, y), f);
+          const int npp = rot_pos(pos_of(x + 1, y), f);
+          c1A.push_back(w.Pt + (size_t)(ym * B + b) * Nc);
+          c1B.push_back(w.X1 + (size_t)((y * 4 + 0) * B + b) * Nc);
+          z1A.push_back(Tp(3 + f, pp, b));
+          z1B.push_back(w.P + (size_t)(ym * B + b) * Nc);
+          z2B.push_back(c.a_rot(site_of(pp), f & 3) + (size_t)b * c.D8());
+          t4A.push_back(w.Pt + (size_t)(y * B + b) * Nc);
+          w1A.push_back(Tp(2 + f, pp, b));
+          w1B.push_back(Cp(3 + f, pp, b));
+          c4B.push_back(w.P + (size_t)(y * B + b) * Nc);
+          sC1.push_back(Cp(0 + f, npp, b));
+          sT4.push_back(Tp(3 + f, npp, b));
+          sC4.push_back(Cp(3 + f, npp, b));
+        }
+      o.c1A = pool.add(c1A); o.c1B = pool.add(c1B); o.z1A = pool.add(z1A); o.z1B = pool.add(z1B);
+      o.z2B = pool.add(z2B); o.t4A = pool.add(t4A); o.w1A = pool.add(w1A); o.w1B = pool.add(w1B);
+      o.c4B = pool.add(c4B); o.sC1 = pool.add(sC1); o.sT4 = pool.add(sT4); o.sC4 = pool.add(sC4);
+    }
+  std::vector<const void*> csA, csS, pA, pU, pS, pV, envC, envT;
+  for (int i = 0; i < 4; ++i)
+    for (int p = 0; p < NPOS; ++p)
+      for (int b = 0; b < B; ++b) {
+        csA.push_back(Cp(i, p, b));
+        csS.push_back(w.cs + (size_t)((i * NPOS + p) * B + b) * chi);
+        envC.push_back(Cp(i, p, b));
+        envT.push_back(Tp(i, p, b));
+      }
+  for (int q = 0; q < 2 * B; ++q) {
+    pA.push_back(w.M + (size_t)q * N2);
+    pU.push_back(w.U + (size_t)q * N2);
+    pS.push_back(w.S + (size_t)q * c.N);
+    pV.push_back(w.V + (size_t)q * N2);
+  }
+  c.off.csA = pool.add(csA); c.off.csS = pool.add(csS);
+  c.off.pA = pool.add(pA); c.off.pU = pool.add(pU); c.off.pS = pool.add(pS); c.off.pV = pool.add(pV);
+  c.off.envC = pool.add(envC); c.off.envT = pool.add(envT);
+}
+
+void ctm_resolve_plans(Ctx& c) {
+  const PtrPool& P = c.pool;
+  for (int f = 0; f < 4; ++f)
+    for (int x = 0; x < 2; ++x) {
+      const MoveOff& o = c.off.mv[f][x];
+      MovePlan& m = c.plan[f][x];
+      m.g1A = P.dev<const cplx* const*>(o.g1A); m.g1B = P.dev<const cplx* const*>(o.g1B);
+      m.g1C = P.dev<cplx* const*>(o.g1C);
+      m.g2A = P.dev<const cplx* const*>(o.g2A); m.g2B = P.dev<const cplx* const*>(o.g2B);
+      m.g2C = P.dev<cplx* const*>(o.g2C);
+      m.g3B = P.dev<const cplx* const*>(o.g3B);
+      m.hA = P.dev<const cplx* const*>(o.hA); m.hB = P.dev<const cplx* const*>(o.hB);
+      m.hC = P.dev<cplx* const*>(o.hC);
+      m.c1A = P.dev<const cplx* const*>(o.c1A); m.c1B = P.dev<const cplx* const*>(o.c1B);
+      m.z1A = P.dev<const cplx* const*>(o.z1A); m.z1B = P.dev<const cplx* const*>(o.z1B);
+      m.z2B = P.dev<const cplx* const*>(o.z2B); m.t4A = P.dev<const cplx* const*>(o.t4A);
+      m.w1A = P.dev<const cplx* const*>(o.w1A); m.w1B = P.dev<const cplx* const*>(o.w1B);
+      m.c4B = P.dev<const cplx* const*>(o.c4B);
+      m.sC1 = P.dev<cplx* const*>(o.sC1); m.sT4 = P.dev<cplx* const*>(o.sT4);
+      m.sC4 = P.dev<cplx* const*>(o.sC4);
+    }
+  c.w.csA = P.dev<const cplx* const*>(c.off.csA);
+  c.w.csS = P.dev<double* const*>(c.off.csS);
+  c.w.pA = P.dev<const cplx* const*>(c.off.pA);
+  c.w.pU = P.dev<cplx* const*>(c.off.pU);
+  c.w.pS = P.dev<double* const*>(c.off.pS);
+  c.w.pV = P.dev<cplx* const*>(c.off.pV);
+  c.w.envC = P.dev<cplx* const*>(c.off.envC);
+  c.w.envT = P.dev<cplx* const*>(c.off.envT);
+}
+
+// ----------------------------------------------------------------------------- small kernels
+// Initial environment: each neighbour's double layer with its outward ket/bra legs traced, zero-
+// padded to chi.  Neighbour offsets: C1 (-1,-1) C2 (1,-1) C3 (1,1) C4 (-1,1) T1 (0,-1) T2 (1,0)
+// T3 (0,1) T4 (-1,0).  Grid: (kind 0..7, pos, b).
+__global__ void env_init_kernel(const cplx* a0A, const cplx* a0B, int B, int D, int chi,
+                                cplx* const* Cout, cplx* const* Tout) {
+  const int D2 = D * D;
+  const int job = blockIdx.x;
+  const int b = job % B, pos = (job / B) % NPOS, kind = job / (B * NPOS);
+  const int x = pos & 1, y = pos >> 1;
+  const int dxs[8] = {-1, 1, 1, -1, 0, 1, 0, -1};
+  const int dys[8] = {-1, -1, 1, 1, -1, 0, 1, 0};
+  const int spos = pos_of(x + dxs[kind] + 2, y + dys[kind] + 2);
+  const long long D8 = (long long)D2 * D2 * D2 * D2;
+  const cplx* a = (site_of(spos) == 0 ? a0A : a0B) + (size_t)b * D8;
+  const int D1 = D + 1;
+#define A4(u, l, d, r) a[(((long long)(u) * D2 + (l)) * D2 + (d)) * D2 + (r)]
+  if (kind < 4) {
+    cplx* out = Cout[(kind * NPOS + pos) * B + b];
+    for (int idx = threadIdx.x; idx < chi * chi; idx += blockDim.x) {
+      const int i = idx / chi, j = idx % chi;
+      cplx acc = cmk(0.0, 0.0);
+      if (i < D2 && j < D2)
+        for (int t1 = 0; t1 < D; ++t1)
+          for (int t2 = 0; t2 < D; ++t2) {
+            const int p = t1 * D1, q = t2 * D1;
+            if (kind == 0) acc = cadd(acc, A4(p, q, i, j));         // C1[D, R], trace U, L
+            else if (kind == 1) acc = cadd(acc, A4(p, i, j, q));    // C2[L, D], trace U, R
+            else if (kind == 2) acc = cadd(acc, A4(i, j, p, q));    // C3[U, L], trace D, R
+            else acc = cadd(acc, A4(j, p, q, i));                   // C4[R, U], trace L, D
+          }
+      out[idx] = acc;
+    }
+  } else {
+    const int e = kind - 4;
+    cplx* out = Tout[(e * NPOS + pos) * B + b];
+    for (int idx = threadIdx.x; idx < chi * D2 * chi; idx += blockDim.x) {
+      const int i = idx / (D2 * chi), k = (idx / chi) % D2, j = idx % chi;
+      cplx acc = cmk(0.0, 0.0);
+      if (i < D2 && j < D2)
+        for (int t1 = 0; t1 < D; ++t1) {
+          const int p = t1 * D1;
+          if (e == 0) acc = cadd(acc, A4(p, i, k, j));              // T1[L, D, R], trace U
+          else if (e == 1) acc = cadd(acc, A4(i, k, j, p));         // T2[U, L, D], trace R
+          else if (e == 2) acc = cadd(acc, A4(k, j, p, i));         // T3[R, U, L], trace D
+          else acc = cadd(acc, A4(j, p, i, k));                     // T4[D, R, U], trace L
+        }
+      out[idx] = acc;
+    }
+  }
+#undef A4
+}
+
+// Projector truncation: singular values of M = R R~ below c.cut_rel (default 1e-10) of the largest
+// are dropped.  Rounding in the singular vectors of M is amplified by ~ eps s_1 / (s_K gap) in the
+// projectors; a larger cutoff (e.g. 1e-6) trades a small truncation bias for a fixed point that does
+// not depend on rounding when the cut falls in a cluster of tiny singular values.
+
+// Projector factors from the SVD of M: rank K (multiplets at the cut kept whole, values below
+// cut_rel of the largest dropped), Vs = V[:, :K] S^{-1/2}, Us = U[:, :K] S^{-1/2}, zero-padded to chi.
+__global__ void proj_prep_kernel(const double* S, const cplx* U, const cplx* V, int N, int chi,
+                                 long long ldu, long long stride_uv, cplx* Us, cplx* Vs, int* kept,
+                                 double degen_rtol, double tiny_rel, double cut_rel) {
+  const int q = blockIdx.x;
+  const double* s = S + (size_t)q * N;
+  __shared__ int sK;
+  if (threadIdx.x == 0) {
+    int K = chi < N ? chi : N;
+    while (K > 1 && K < N && s[K] > tiny_rel * s[0] && s[K - 1] / s[K] - 1.0 < degen_rtol) --K;
+    int cnt = 0;
+    for (int j = 0; j < K; ++j) cnt += s[j] > cut_rel * s[0];
+    K = cnt < K ? cnt : K;
+    if (!(s[0] > 0.0)) K = 0;
+    else if (K < 1) K = 1;
+    sK = K;
+    kept[q] = K;
+  }
+  __syncthreads();
+  const int K = sK;
+  const cplx* Uq = U + (size_t)q * stride_uv;
+  const cplx* Vq = V + (size_t)q * stride_uv;
+  cplx* Uo = Us + (size_t)q * N * chi;
+  cplx* Vo = Vs + (size_t)q * N * chi;
+  for (int idx = threadIdx.x; idx < N * chi; idx += blockDim.x) {
+    const int i = idx / chi, j = idx % chi;
+    if (j < K) {
+      const double f = 1.0 / sqrt(s[j]);
+      Uo[idx] = cscale(Uq[(size_t)i * ldu + j], f);
+      Vo[idx] = cscale(Vq[(size_t)i * ldu + j], f);
+    } else {
+      Uo[idx] = cmk(0.0, 0.0);
+      Vo[idx] = cmk(0.0, 0.0);
+    }
+  }
+}
+
+// Divide each new tensor by its largest modulus and store it into its environment slot, except for
+// instances whose environment has already converged.  Grid: (tensor kind 0..2, problem q < 2B).
+__global__ void normalize_store_kernel(const cplx* C1n, const cplx* T4n, const cplx* C4n, int B,
+                                       long long nC, long long nT, cplx* const* sC1, cplx* const* sT4,
+                                       cplx* const* sC4, const int* frozen, unsigned* err) {
+  const int kind = blockIdx.x / (2 * B), q = blockIdx.x % (2 * B), b = q % B;
+  if (frozen[b]) return;
+  const long long n = kind == 1 ? nT : nC;
+  const cplx* src = (kind == 0 ? C1n : kind == 1 ? T4n : C4n) + (size_t)q * n;
+  cplx* dst = (kind == 0 ? sC1 : kind == 1 ? sT4 : sC4)[q];
+  __shared__ double red[256];
+  double m = 0.0;
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, cabs2(src[i]));
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]);
+    __syncthreads();
+  }
+  const double mx = sqrt(red[0]);
+  if (!isfinite(mx) && threadIdx.x == 0) atomicOr(err, (unsigned)DEV_NONFINITE);
+  const double f = mx > 0.0 ? 1.0 / mx : 0.0;
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) dst[i] = cscale(src[i], f);
+}
+
+// Convergence number per instance: max over the 16 corners of || s/s_1 - s_prev/s_1,prev ||_2.
+// first != 0 only records the spectra of the starting environment.
+__global__ void spectra_delta_kernel(const double* cs, double* prev, int B, int chi, int first,
+                                     double tol, double* delta, int* frozen, int* sweeps) {
+  const int b = blockIdx.x;
+  __shared__ double dmax[16];
+  const int c = threadIdx.x;
+  if (frozen[b]) return;
+  if (c < 16) {
+    const double* s = cs + (size_t)(c * B + b) * chi;
+    double* p = prev + (size_t)(c * B + b) * chi;
+    const double s0 = s[0];
+    double acc = 0.0;
+    for (int k = 0; k < chi; ++k) {
+      const double v = s0 > 0.0 ? s[k] / s0 : 0.0;
+      const double dv = v - p[k];
+      acc += dv * dv;
+      p[k] = v;
+    }
+    dmax[c] = sqrt(acc);
+  }
+  __syncthreads();
+  if (c == 0 && !first) {
+    double m = 0.0;
+    for (int k = 0; k < 16; ++k) m = fmax(m, dmax[k]);
+    if (!(m == m)) m = INFINITY;
+    delta[b] = m;
+    sweeps[b] += 1;
+    if (m < tol) frozen[b] = 1;
+  }
+}
+
+// ----------------------------------------------------------------------------- drivers
+int ctm_prepare_tensors(Ctx& c) {
+  if (int rc = physical_tensors(c.GA, c.GB, c.lam, c.Aph, c.Bph, c.d, c.D, c.B, c.st)) return rc;
+  if (int rc = double_layers(c.Aph, c.a_rot(0, 0), c.d, c.D, c.B, 4, c.st)) return rc;
+  if (int rc = double_layers(c.Bph, c.a_rot(1, 0), c.d, c.D, c.B, 4, c.st)) return rc;
+  return 0;
+}
+
+int ctm_init_env(Ctx& c) {
+  env_init_kernel<<<8 * NPOS * c.B, 256, 0, c.st>>>(c.a_rot(0, 0), c.a_rot(1, 0), c.B, c.D, c.chi,
+                                                    c.w.envC, c.w.envT);
+  IPEPS_CUDA_TRY(cudaGetLastError());
+  c.env_valid = true;
+  return 0;
+}
+
+static GemmDesc gd(int M, int N, int K, int batch) {
+  GemmDesc g;
+  memset(&g, 0, sizeof(g));
+  g.M = M; g.N = N; g.K = K; g.batch = batch;
+  g.opA = OP_N; g.opB = OP_N;
+  g.alpha = cmk(1.0, 0.0); g.beta = cmk(0.0, 0.0);
+  return g;
+}
+
+static int left_move(Ctx& c, int f, int x) {
+  const MovePlan& m = c.plan[f][x];
+  CtmWork& w = c.w;
+  const int B = c.B, chi = c.chi, D2 = c.D2, N = c.N;
+  const long long N2 = c.N2(), Nc = (long long)N * chi, chi2 = (long long)chi * chi;
+  const long long T = (long long)chi * D2 * chi;
+  cudaStream_t st = c.st;
+  int rc;
+  // enlarged corners (8B problems)
+  GemmDesc g = gd(chi, D2 * chi, chi, 8 * B);
+  g.Aptr = m.g1A; g.Bptr = m.g1B; g.Cptr = m.g1C; g.lda = chi; g.ldb = D2 * chi; g.ldc = D2 * chi;
+  if ((rc = zgemm_f64(g, st))) return rc;
+  g = gd(chi * D2, D2 * chi, chi, 8 * B);
+  g.Aptr = m.g2A; g.Bptr = m.g2B; g.Cptr = m.g2C; g.lda = chi; g.ldb = D2 * chi; g.ldc = D2 * chi;
+  if ((rc = zgemm_f64(g, st))) return rc;
+  {
+    const int dims[4] = {chi, D2, D2, chi}, perm[4] = {0, 3, 2, 1};
+    if ((rc = permute_c128(w.X2, w.X2p, 4, dims, perm, 8 * B, N2, N2, st))) return rc;
+  }
+  g = gd(chi * chi, D2 * D2, D2 * D2, 8 * B);
+  g.A = w.X2p; g.sA = N2; g.lda = D2 * D2;
+  g.Bptr = m.g3B; g.ldb = D2 * D2;
+  g.C = w.Y; g.sC = N2; g.ldc = D2 * D2;
+  if ((rc = zgemm_f64(g, st))) return rc;
+  {
+    const int dims[4] = {chi, chi, D2, D2}, perm[4] = {0, 2, 1, 3};
+    if ((rc = permute_c128(w.Y, w.Q, 4, dims, perm, 8 * B, N2, N2, st))) return rc;
+  }
+  // halves and the product over the cut
+  g = gd(N, N, N, 4 * B);
+  g.Aptr = m.hA; g.Bptr = m.hB; g.Cptr = m.hC; g.lda = N; g.ldb = N; g.ldc = N;
+  if ((rc = zgemm_f64(g, st))) return rc;
+  cplx* Rt = w.H;
+  cplx* R = w.H + (size_t)2 * B * N2;
+  g = gd(N, N, N, 2 * B);
+  g.A = R; g.sA = N2; g.lda = N; g.B = Rt; g.sB = N2; g.ldb = N; g.C = w.M; g.sC = N2; g.ldc = N;
+  if ((rc = zgemm_f64(g, st))) return rc;
+  // projector SVD (full one-sided Jacobi of M)
+  SvdDesc sd;
+  sd.m = N; sd.n = N; sd.batch = 2 * B;
+  sd.A = w.pA; sd.lda = N; sd.U = w.pU; sd.ldu = N; sd.S = w.pS; sd.V = w.pV; sd.ldv = N;
+  sd.tol = 4e-16 * N; sd.max_sweeps = 80; sd.err = c.derr; sd.sweeps_out = nullptr;
+  if ((rc = jacobi_svd(sd, st))) return rc;
+  proj_prep_kernel<<<2 * B, 256, 0, st>>>(w.S, w.U, w.V, N, chi, N, N2, w.Us, w.Vs, w.kept, 1e-10,
+                                          1e-14, c.cut_rel);
+  IPEPS_CUDA_TRY(cudaGetLastError());
+  g = gd(N, chi, N, 2 * B);     // P = R~ Vs
+  g.A = Rt; g.sA = N2; g.lda = N; g.B = w.Vs; g.sB = Nc; g.ldb = chi; g.C = w.P; g.sC = Nc; g.ldc = chi;
+  if ((rc = zgemm_f64(g, st))) return rc;
+  g = gd(chi, N, N, 2 * B);     // P~ = Us^+ R
+  g.opA = OP_C; g.A = w.Us; g.sA = Nc; g.lda = chi;
+  g.B = R; g.sB = N2; g.ldb = N; g.C = w.Pt; g.sC = Nc; g.ldc = N;
+  if ((rc = zgemm_f64(g, st))) return rc;
+  // absorption: C1' = P~[y-1] (C1 T1)
+  g = gd(chi, chi, N, 2 * B);
+  g.Aptr = m.c1A; g.lda = N; g.Bptr = m.c1B; g.ldb = chi; g.C = w.C1n; g.sC = chi2; g.ldc = chi;
+  if ((rc = zgemm_f64(g, st))) return rc;
+  // T4' = P~[y] (T4 a) P[y-1]
+  g = gd(chi * D2, D2 * chi, chi, 2 * B);
+  g.Aptr = m.z1A; g.lda = chi; g.Bptr = m.z1B; g.ldb = D2 * chi; g.C = w.Z1; g.sC = N2; g.ldc = D2 * chi;
+  if ((rc = zgemm_f64(g, st))) return rc;
+  {
+    const int dims[4] = {chi, D2, D2, chi}, perm[4] = {0, 3, 2, 1};
+    if ((rc = permute_c128(w.Z1, w.Z1p, 4, dims, perm, 2 * B, N2, N2, st))) return rc;
+  }
+  g = gd(chi * chi, D2 * D2, D2 * D2, 2 * B);
+  g.A = w.Z1p; g.sA = N2; g.lda = D2 * D2; g.Bptr = m.z2B; g.ldb = D2 * D2;
+  g.C = w.Z2; g.sC = N2; g.ldc = D2 * D2;
+  if ((rc = zgemm_f64(g, st))) return rc;
+  {
+    const int dims[4] = {chi, chi, D2, D2}, perm[4] = {0, 2, 3, 1};
+    if ((rc = permute_c128(w.Z2, w.Z2p, 4, dims, perm, 2 * B, N2, N2, st))) return rc;
+  }
+  g = gd(chi, D2 * chi, N, 2 * B);
+  g.Aptr = m.t4A; g.lda = N; g.B = w.Z2p; g.sB = N2; g.ldb = D2 * chi; g.C = w.T4n; g.sC = T;
+  g.ldc = D2 * chi;
+  if ((rc = zgemm_f64(g, st))) return rc;
+  // C4' = (T3 C4) P[y]
+  g = gd(chi * D2, chi, chi, 2 * B);
+  g.Aptr = m.w1A; g.lda = chi; g.Bptr = m.w1B; g.ldb = chi; g.C = w.W1; g.sC = T; g.ldc = chi;
+  if ((rc = zgemm_f64(g, st))) return rc;
+  {
+    const int dims[3] = {chi, D2, chi}, perm[3] = {0, 2, 1};
+    if ((rc = permute_c128(w.W1, w.W1p, 3, dims, perm, 2 * B, T, T, st))) return rc;
+  }
+  g = gd(chi, chi, N, 2 * B);
+  g.A = w.W1p; g.sA = T; g.lda = N; g.Bptr = m.c4B; g.ldb = chi; g.C = w.C4n; g.sC = chi2; g.ldc = chi;
+  if ((rc = zgemm_f64(g, st))) return rc;
+  normalize_store_kernel<<<3 * 2 * B, 256, 0, st>>>(w.C1n, w.T4n, w.C4n, B, chi2, T, m.sC1, m.sT4,
+                                                   m.sC4, w.frozen, c.derr);
+  IPEPS_CUDA_TRY(cudaGetLastError());
+  return 0;
+}
+
+int ctm_sweep(Ctx& c) {
+  for (int f = 0; f < 4; ++f)
+    for (int x = 0; x < 2; ++x)
+      if (int rc = left_move(c, f, x)) return rc;
+  return 0;
+}
+
+int ctm_spectra(Ctx& c, double tol, int first) {
+  SvdDesc sd;
+  sd.m = c.chi; sd.n = c.chi; sd.batch = 16 * c.B;
+  sd.A = c.w.csA; sd.lda = c.chi; sd.U = nullptr; sd.ldu = 0; sd.S = c.w.csS; sd.V = nullptr; sd.ldv = 0;
+  sd.tol = 4e-16 * c.chi; sd.max_sweeps = 80; sd.err = c.derr; sd.sweeps_out = nullptr;
+  if (int rc = jacobi_svd(sd, c.st)) return rc;
+  spectra_delta_kernel<<<c.B, 32, 0, c.st>>>(c.w.cs, c.w.prev, c.B, c.chi, first, tol, c.w.delta,
+                                             c.w.frozen, c.w.sweeps);
+  IPEPS_CUDA_TRY(cudaGetLastError());
+  return 0;
+}
+
+}  // namespace ipeps

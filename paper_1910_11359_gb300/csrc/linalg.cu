@@ -1,0 +1,348 @@
+// FP64 dense building blocks (see linalg.cuh).
+#include <cooperative_groups.h>
+
+#include <algorithm>
+
+#include "linalg.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace ipeps {
+
+// ------------------------------------------------------------------------------------ GEMM
+// 16 x 16 output tile per CTA, one complex output per thread, K staged through shared memory in
+// chunks of 16.  FP64 issue rate on this part is ~2 DFMA/clk/SM, far below what shared memory can
+// feed, so small tiles (little padding waste at N = 32..162) cost nothing in throughput.
+constexpr int GT = 16;
+
+__device__ __forceinline__ cplx load_op(const cplx* P, long long ld, int op, int row, int col) {
+  // element (row, col) of op(P)
+  if (op == OP_N) return P[(long long)row * ld + col];
+  cplx v = P[(long long)col * ld + row];
+  return op == OP_C ? cconj(v) : v;
+}
+
+__global__ void __launch_bounds__(GT * GT) zgemm_kernel(GemmDesc g) {
+  const int b = blockIdx.z;
+  const cplx* A = g.Aptr ? g.Aptr[b] : g.A + (long long)b * g.sA;
+  const cplx* B = g.Bptr ? g.Bptr[b] : g.B + (long long)b * g.sB;
+  cplx* C = g.Cptr ? g.Cptr[b] : g.C + (long long)b * g.sC;
+  __shared__ cplx As[GT][GT + 1];
+  __shared__ cplx Bs[GT][GT + 1];
+  const int tx = threadIdx.x % GT, ty = threadIdx.x / GT;
+  const int m0 = blockIdx.y * GT, n0 = blockIdx.x * GT;
+  cplx acc = cmk(0.0, 0.0);
+  for (int k0 = 0; k0 < g.K; k0 += GT) {
+    {  // A tile As[mm][kk]; for transposed storage let consecutive threads walk the stored row
+      int mm, kk;
+      if (g.opA == OP_N) { mm = ty; kk = tx; } else { mm = tx; kk = ty; }
+      int gm = m0 + mm, gk = k0 + kk;
+      As[mm][kk] = (gm < g.M && gk < g.K) ? load_op(A, g.lda, g.opA, gm, gk) : cmk(0.0, 0.0);
+    }
+    {  // B tile Bs[kk][nn]
+      int kk, nn;
+      if (g.opB == OP_N) { kk = ty; nn = tx; } else { kk = tx; nn = ty; }
+      int gk = k0 + kk, gn = n0 + nn;
+      Bs[kk][nn] = (gk < g.K && gn < g.N) ? load_op(B, g.ldb, g.opB, gk, gn) : cmk(0.0, 0.0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GT; ++kk) cfma(acc, As[ty][kk], Bs[kk][tx]);
+    __syncthreads();
+  }
+  const int gm = m0 + ty, gn = n0 + tx;
+  if (gm < g.M && gn < g.N) {
+    cplx r = cmul(g.alpha, acc);
+    long long o = (long long)gm * g.ldc + gn;
+    if (g.beta.x != 0.0 || g.beta.y != 0.0) r = cadd(r, cmul(g.beta, C[o]));
+    C[o] = r;
+  }
+}
+
+int zgemm_f64(const GemmDesc& g, cudaStream_t st) {
+  if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return 0;
+  if (g.batch > 65535) return cuda_fail(cudaErrorInvalidValue, "zgemm batch", __FILE__, __LINE__);
+  dim3 grid((g.N + GT - 1) / GT, (g.M + GT - 1) / GT, g.batch);
+  zgemm_kernel<<<grid, GT * GT, 0, st>>>(g);
+  IPEPS_CUDA_TRY(cudaGetLastError());
+  return 0;
+}
+
+// ------------------------------------------------------------------------------------ permute
+struct PermArgs {
+  int rank;
+  long long out_dims[8];
+  long long in_stride_of_out_axis[8];
+};
+
+__global__ void permute_kernel(const cplx* __restrict__ in, cplx* __restrict__ out, PermArgs a,
+                               long long total, int batch, long long s_in, long long s_out) {
+  long long n = total * batch;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+       idx += (long long)gridDim.x * blockDim.x) {
+    long long b = idx / total, o = idx - b * total;
+    long long rem = o, off = 0;
+    for (int j = a.rank - 1; j >= 0; --j) {
+      long long c = rem % a.out_dims[j];
+      rem /= a.out_dims[j];
+      off += c * a.in_stride_of_out_axis[j];
+    }
+    out[b * s_out + o] = in[b * s_in + off];
+  }
+}
+
+int permute_c128(const cplx* in, cplx* out, int rank, const int* dims, const int* perm, int batch,
+                 long long s_in, long long s_out, cudaStream_t st) {
+  if (rank < 1 || rank > 8) return cuda_fail(cudaErrorInvalidValue, "permute rank", __FILE__, __LINE__);
+  PermArgs a;
+  a.rank = rank;
+  long long in_stride[8];
+  long long s = 1;
+  for (int j = rank - 1; j >= 0; --j) { in_stride[j] = s; s *= dims[j]; }
+  long long total = s;
+  for (int j = 0; j < rank; ++j) {
+    a.out_dims[j] = dims[perm[j]];
+    a.in_stride_of_out_axis[j] = in_stride[perm[j]];
+  }
+  long long n = total * batch;
+  if (n == 0) return 0;
+  int threads = 256;
+  long long blocks = std::min<long long>((n + threads - 1) / threads, 152LL * 16);
+  permute_kernel<<<(unsigned)blocks, threads, 0, st>>>(in, out, a, total, batch, s_in, s_out);
+  IPEPS_CUDA_TRY(cudaGetLastError());
+  return 0;
+}
+
+// ------------------------------------------------------------------------------------ Jacobi SVD
+constexpr int JCS = 8;          // CTAs per cluster (portable cluster size)
+// Columns whose squared norm is below JTINY take part in no rotation: their squared entries sit in
+// or near the subnormal range, where the rotation's phase cannot be formed accurately.
+constexpr double JTINY = 1e-250;
+constexpr int JTHREADS = 256;
+
+struct JacobiArgs {
+  SvdDesc d;
+  int np, ra, rw;
+};
+
+// Round-robin ("circle") tournament: position 0 fixed, the rest rotate by one each round, so every
+// pair of the np (even) columns meets exactly once in np - 1 rounds.
+__device__ __forceinline__ int rr_pos(int i, int r, int np) {
+  return i == 0 ? 0 : ((i - 1 + r) % (np - 1)) + 1;
+}
+
+__global__ void __cluster_dims__(JCS, 1, 1) __launch_bounds__(JTHREADS)
+jacobi_kernel(JacobiArgs args) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const SvdDesc& d = args.d;
+  const int rank = (int)cluster.block_rank();
+  const int prob = blockIdx.x / JCS;
+  const int np = args.np, ra = args.ra, rw = args.rw;
+  const int npairs = np / 2;
+  const int m = d.m, n = d.n;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = JTHREADS / 32;
+
+  extern __shared__ __align__(16) unsigned char jsm_raw[];
+  cplx* colA = reinterpret_cast<cplx*>(jsm_raw);           // colA[j * ra + i]
+  cplx* colW = colA + (size_t)np * ra;                      // colW[j * rw + i]
+  double* part = reinterpret_cast<double*>(colW + (size_t)np * rw);   // [2][npairs][4]
+  double* rot = part + 2 * npairs * 4;                      // [npairs][4]: c, s, er, ei
+  int* flags = reinterpret_cast<int*>(rot + npairs * 4);    // [npairs] + any + nonfinite
+
+  const cplx* A = d.A[prob];
+  const int a0 = rank * ra, w0 = rank * rw;
+  for (int idx = tid; idx < np * ra; idx += JTHREADS) {
+    int j = idx / ra, i = idx - j * ra, gi = a0 + i;
+    colA[idx] = (j < n && gi < m) ? A[(long long)gi * d.lda + j] : cmk(0.0, 0.0);
+  }
+  for (int idx = tid; idx < np * rw; idx += JTHREADS) {
+    int j = idx / rw, i = idx - j * rw, gi = w0 + i;
+    colW[idx] = (gi == j && gi < n) ? cmk(1.0, 0.0) : cmk(0.0, 0.0);
+  }
+  if (tid == 0) { flags[npairs] = 0; flags[npairs + 1] = 0; }
+  __syncthreads();
+
+  const int nrounds = np - 1;
+  long long gcount = 0;
+  int sweep = 0;
+  bool converged = false;
+  for (sweep = 0; sweep < d.max_sweeps; ++sweep) {
+    for (int r = 0; r < nrounds; ++r, ++gcount) {
+      const int buf = (int)(gcount & 1);
+      double* mypart = part + buf * npairs * 4;
+      for (int p = warp; p < npairs; p += nwarps) {
+        const int cp = rr_pos(p, r, np), cq = rr_pos(np - 1 - p, r, np);
+        double al = 0.0, be = 0.0, gr = 0.0, gi = 0.0;
+        for (int i = lane; i < ra; i += 32) {
+          cplx x = colA[cp * ra + i], y = colA[cq * ra + i];
+          al = fma(x.x, x.x, fma(x.y, x.y, al));
+          be = fma(y.x, y.x, fma(y.y, y.y, be));
+          gr = fma(x.x, y.x, fma(x.y, y.y, gr));
+          gi = fma(x.x, y.y, fma(-x.y, y.x, gi));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+          be += __shfl_xor_sync(0xffffffffu, be, o);
+          gr += __shfl_xor_sync(0xffffffffu, gr, o);
+          gi += __shfl_xor_sync(0xffffffffu, gi, o);
+        }
+        if (lane == 0) {
+          mypart[p * 4 + 0] = al; mypart[p * 4 + 1] = be;
+          mypart[p * 4 + 2] = gr; mypart[p * 4 + 3] = gi;
+        }
+      }
+      cluster.sync();
+      // every CTA sums the partials in rank order, so all CTAs reach bit-identical decisions
+      for (int p = tid; p < npairs; p += JTHREADS) {
+        double al = 0.0, be = 0.0, gr = 0.0, gi = 0.0;
+        for (int q = 0; q < JCS; ++q) {
+          const double* rp = cluster.map_shared_rank(part, q) + buf * npairs * 4 + p * 4;
+          al += rp[0]; be += rp[1]; gr += rp[2]; gi += rp[3];
+        }
+        const double g = sqrt(gr * gr + gi * gi);
+        int doit = 0;
+        if (!(isfinite(al) && isfinite(be) && isfinite(g))) {
+          flags[npairs + 1] = 1;
+        } else if (al > JTINY && be > JTINY && g > d.tol * sqrt(al) * sqrt(be)) {
+          const double zeta = (be - al) / (2.0 * g);
+          const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + hypot(1.0, zeta));
+          const double c = 1.0 / sqrt(1.0 + t * t);
+          // phase conj(gamma)/|gamma| from the rescaled components (no precision loss when the
+          // components of gamma are small)
+          const double mg = fmax(fabs(gr), fabs(gi));
+          const double grs = gr / mg, gis = gi / mg;
+          const double gn = sqrt(grs * grs + gis * gis);
+          rot[p * 4 + 0] = c;
+          rot[p * 4 + 1] = c * t;
+          rot[p * 4 + 2] = grs / gn;
+          rot[p * 4 + 3] = -gis / gn;
+          doit = 1;
+          flags[npairs] = 1;
+        }
+        flags[p] = doit;
+      }
+      __syncthreads();
+      if (flags[npairs + 1]) break;
+      const int rows = ra + rw;
+      for (int idx = tid; idx < npairs * rows; idx += JTHREADS) {
+        const int p = idx / rows, i = idx - p * rows;
+        if (!flags[p]) continue;
+        const int cp = rr_pos(p, r, np), cq = rr_pos(np - 1 - p, r, np);
+        cplx* base = i < ra ? colA : colW;
+        const int st = i < ra ? ra : rw;
+        const int ii = i < ra ? i : i - ra;
+        const double c = rot[p * 4 + 0], s = rot[p * 4 + 1];
+        const cplx e = cmk(rot[p * 4 + 2], rot[p * 4 + 3]);
+        const cplx x = base[cp * st + ii];
+        const cplx ey = cmul(e, base[cq * st + ii]);
+        base[cp * st + ii] = cmk(c * x.x - s * ey.x, c * x.y - s * ey.y);
+        base[cq * st + ii] = cmk(s * x.x + c * ey.x, s * x.y + c * ey.y);
+      }
+      __syncthreads();
+    }
+    const bool nonfinite = flags[npairs + 1] != 0;
+    const bool any = flags[npairs] != 0;
+    __syncthreads();
+    if (tid == 0) flags[npairs] = 0;
+    __syncthreads();
+    if (nonfinite) break;
+    if (!any) { converged = true; break; }
+  }
+  const bool nonfinite_any = flags[npairs + 1] != 0;
+  // column norms, reduced over the cluster; the barrier first lets every CTA finish reading the
+  // partial-sum buffers of the last round
+  cluster.sync();
+  double* norms = part;                                       // np doubles fit (8 * npairs >= np)
+  for (int j = warp; j < np; j += nwarps) {
+    double s = 0.0;
+    for (int i = lane; i < ra; i += 32) s += cabs2(colA[j * ra + i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) norms[j] = s;
+  }
+  cluster.sync();
+  // rot[] is free now: sigma in rot[0..np), sorted source column in flags[0..np) (both fit)
+  double* sig = rot;
+  int* order = flags;
+  __syncthreads();
+  for (int j = tid; j < np; j += JTHREADS) {
+    double s = 0.0;
+    for (int q = 0; q < JCS; ++q) s += cluster.map_shared_rank(norms, q)[j];
+    sig[j] = sqrt(s);
+  }
+  __syncthreads();
+  for (int j = tid; j < n; j += JTHREADS) {
+    int rk = 0;
+    for (int k = 0; k < n; ++k) rk += (sig[k] > sig[j]) || (sig[k] == sig[j] && k < j);
+    order[rk] = j;
+  }
+  __syncthreads();
+  if (d.S && rank == 0)
+    for (int j = tid; j < n; j += JTHREADS) d.S[prob][j] = sig[order[j]];
+  if (d.U) {
+    cplx* U = d.U[prob];
+    for (int idx = tid; idx < n * ra; idx += JTHREADS) {
+      const int j = idx / ra, i = idx - j * ra, gi = a0 + i;
+      if (gi >= m) continue;
+      const double s = sig[order[j]];
+      const cplx v = colA[order[j] * ra + i];
+      U[(long long)gi * d.ldu + j] = s > 0.0 ? cscale(v, 1.0 / s) : cmk(0.0, 0.0);
+    }
+  }
+  if (d.V) {
+    cplx* V = d.V[prob];
+    for (int idx = tid; idx < n * rw; idx += JTHREADS) {
+      const int j = idx / rw, i = idx - j * rw, gi = w0 + i;
+      if (gi >= n) continue;
+      V[(long long)gi * d.ldv + j] = colW[order[j] * rw + i];
+    }
+  }
+  if (tid == 0 && rank == 0) {
+    if (d.sweeps_out) d.sweeps_out[prob] = sweep + 1;
+    if (d.err) {
+      if (nonfinite_any) atomicOr(d.err, (unsigned)DEV_NONFINITE);
+      else if (!converged) atomicOr(d.err, (unsigned)DEV_JACOBI_CAP);
+    }
+  }
+  cluster.sync();   // no CTA leaves while its shared memory may still be read by the others
+}
+
+static void jacobi_layout(int m, int n, int* np, int* ra, int* rw) {
+  *np = n + (n & 1);
+  *ra = (m + JCS - 1) / JCS;
+  *rw = (n + JCS - 1) / JCS;
+}
+
+size_t jacobi_svd_smem_bytes(int m, int n) {
+  int np, ra, rw;
+  jacobi_layout(m, n, &np, &ra, &rw);
+  size_t npairs = np / 2;
+  return (size_t)np * (ra + rw) * sizeof(cplx) + (2 * npairs * 4 + npairs * 4) * sizeof(double) +
+         (npairs + 2 + np) * sizeof(int) + 64;
+}
+
+bool jacobi_svd_fits(int m, int n) {
+  return m >= n && n >= 1 && jacobi_svd_smem_bytes(m, n) <= 200 * 1024;
+}
+
+int jacobi_svd(const SvdDesc& d, cudaStream_t st) {
+  if (d.batch <= 0) return 0;
+  if (!jacobi_svd_fits(d.m, d.n))
+    return cuda_fail(cudaErrorInvalidValue, "jacobi_svd size", __FILE__, __LINE__);
+  JacobiArgs a;
+  a.d = d;
+  jacobi_layout(d.m, d.n, &a.np, &a.ra, &a.rw);
+  size_t smem = jacobi_svd_smem_bytes(d.m, d.n);
+  static bool attr_set = false;
+  if (!attr_set) {
+    IPEPS_CUDA_TRY(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        200 * 1024 + 1024));
+    attr_set = true;
+  }
+  jacobi_kernel<<<d.batch * JCS, JTHREADS, smem, st>>>(a);
+  IPEPS_CUDA_TRY(cudaGetLastError());
+  return 0;
+}
+
+}  // namespace ipeps

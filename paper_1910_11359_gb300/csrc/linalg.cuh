@@ -1,0 +1,51 @@
+// FP64 dense building blocks: batched complex GEMM, tensor permutation, cluster one-sided Jacobi SVD.
+#pragma once
+#include "common.cuh"
+
+namespace ipeps {
+
+enum Op : int { OP_N = 0, OP_T = 1, OP_C = 2 };
+
+// One batched complex GEMM description: for b in [0, batch):
+//   C[b] = alpha * op(A[b]) * op(B[b]) + beta * C[b]       (row-major, leading dimensions lda..ldc)
+// op(A) is M x K: OP_N reads A[m*lda + k]; OP_T reads A[k*lda + m]; OP_C reads conj(A[k*lda + m]).
+// op(B) is K x N: OP_N reads B[k*ldb + n]; OP_T reads B[n*ldb + k]; OP_C reads conj(B[n*ldb + k]).
+// Pointers are either strided (base + b * stride) or taken from device pointer arrays (ptrs != 0).
+struct GemmDesc {
+  int M, N, K, batch;
+  int opA, opB;
+  long long lda, ldb, ldc;
+  long long sA, sB, sC;           // batch strides in elements (used when the pointer arrays are null)
+  const cplx* A; const cplx* B; cplx* C;
+  const cplx* const* Aptr; const cplx* const* Bptr; cplx* const* Cptr;
+  cplx alpha, beta;
+};
+
+int zgemm_f64(const GemmDesc& g, cudaStream_t st);
+
+// out = permute(in): out axis j is in axis perm[j]; rank <= 8; batched with element strides.
+int permute_c128(const cplx* in, cplx* out, int rank, const int* dims, const int* perm, int batch,
+                 long long s_in, long long s_out, cudaStream_t st);
+
+// One-sided (Hestenes) Jacobi SVD of a batch of m x n complex matrices (m >= n), A = U S V^+.
+// Each problem is handled by one thread-block cluster whose CTAs own disjoint row slices of [A; W]
+// in shared memory; pair dot products are reduced across the cluster through distributed shared
+// memory.  Singular values are sorted in descending order.  U (m x n, row-major, may be null),
+// V (n x n row-major with V[i*ldv + j] = V_ij, may be null).
+struct SvdDesc {
+  int m, n, batch;
+  const cplx* const* A; long long lda;
+  cplx* const* U; long long ldu;
+  double* const* S;
+  cplx* const* V; long long ldv;
+  double tol;          // rotate a pair when |a_p^+ a_q| > tol * ||a_p|| ||a_q||
+  int max_sweeps;
+  unsigned* err;       // device error word (DevErr bits)
+  int* sweeps_out;     // optional: sweeps used per problem
+};
+
+int jacobi_svd(const SvdDesc& d, cudaStream_t st);
+size_t jacobi_svd_smem_bytes(int m, int n);
+bool jacobi_svd_fits(int m, int n);
+
+}  // namespace ipeps

@@ -1,0 +1,281 @@
+// Readout from the converged environment (paper Sec. "Set up for iPEPS", Readout: local expectation
+// values of |Psi(t)> are exact disorder averages with the auxiliaries traced out; Sec. "Results for
+// interacting case": imbalance I = n_A - n_B).
+//
+// Every reduced density matrix is assembled from "left halves": in rotated frame f, at logical
+// position q, with the open (ket x bra) site tensor,
+//   Lh[e3r, c1r, s, s', kR] = C1 T1 T4 C4 T3 (around q) x ao[s, s', kU, kL, kD, kR]
+// where e3r / c1r are the right ends of T3 / T1 and kR the open right leg.
+//   rho1(q)          = Lh_f0(q) . (C2 T2 C3)(q)                          (A at (0,0), B at (1,0))
+//   rho_h(p -> p+x)  = Lh_f0(p) . Lh_f2(p+x)                              (the right half is a left
+//   rho_v(p -> p+y)  = Lh_f1(rot p) . Lh_f3(rot^3 (p+y))                   half rotated by 180 deg)
+// The eight left halves needed (frames 0..3 x logical positions (0,0) [site A], (1,0) [site B])
+// are computed as one batch.
+#include <vector>
+
+#include "ctx.cuh"
+#include "measure.cuh"
+
+namespace ipeps {
+
+// open double layer, rotated and reshaped for the last contraction:
+// aoP[(i0 i1 i2), (s s' i3)] = rot^f(ao)[s, s', i0, i1, i2, i3], ao = A (x) conj(A) per leg
+__global__ void open_layer_kernel(const cplx* A, int d, int D, int B, int site_f_count, int f_of0,
+                                  cplx* out, int f) {
+  const int D2 = D * D, D4 = D2 * D2;
+  const long long rows = (long long)D2 * D2 * D2, cols = (long long)d * d * D2;
+  const long long per = rows * cols;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < (long long)B * per;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(idx / per);
+    const long long r = (idx % per) / cols, cc = idx % cols;
+    int p[4];
+    p[0] = (int)(r / (D2 * D2)); p[1] = (int)((r / D2) % D2); p[2] = (int)(r % D2);
+    const int s = (int)(cc / (d * D2)), sp = (int)((cc / D2) % d);
+    p[3] = (int)(cc % D2);
+    int ket = 0, bra = 0;
+    for (int j = 0; j < 4; ++j) {
+      const int q = p[(j + f) & 3];       // leg j of the unrotated tensor
+      ket = ket * D + q / D;
+      bra = bra * D + q % D;
+    }
+    const cplx* Ab = A + (size_t)b * d * D4;
+    out[idx] = cmulc(Ab[(size_t)sp * D4 + bra], Ab[(size_t)s * D4 + ket]);
+  }
+}
+
+// rho1[q][s][s'] = sum_{a,b,k} Lh[a, b, s, s', k] RC[b, k, a];  one CTA per (site, b)
+__global__ void rho1_kernel(const cplx* Lh, const cplx* RC, int chi, int D2, int d, cplx* rho) {
+  const int q = blockIdx.x;
+  const long long per = (long long)chi * chi * d * d * D2;
+  const cplx* L = Lh + (size_t)q * per;
+  const cplx* R = RC + (size_t)q * chi * D2 * chi;
+  __shared__ cplx red[256];
+  for (int ss = 0; ss < d * d; ++ss) {
+    cplx acc = cmk(0.0, 0.0);
+    for (long long t = threadIdx.x; t < (long long)chi * chi * D2; t += blockDim.x) {
+      const int a = (int)(t / (chi * D2)), bb = (int)((t / D2) % chi), k = (int)(t % D2);
+      cfma(acc, L[(((size_t)a * chi + bb) * d * d + ss) * D2 + k], R[((size_t)bb * D2 + k) * chi + a]);
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if (threadIdx.x < o) red[threadIdx.x] = cadd(red[threadIdx.x], red[threadIdx.x + o]);
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) rho[(size_t)q * d * d + ss] = red[0];
+    __syncthreads();
+  }
+}
+
+// rho2[s, s', v, v'] = sum_{a,b,k} Lh1[a, b, s, s', k] Lh2[b, a, v, v', k]; one CTA per output entry
+__global__ void rho2_kernel(const cplx* const* L1, const cplx* const* L2, int chi, int D2, int d,
+                            cplx* rho) {
+  const int d2 = d * d;
+  const int job = blockIdx.x / (d2 * d2), e = blockIdx.x % (d2 * d2);
+  const int ss = e / d2, vv = e % d2;
+  const cplx* X = L1[job];
+  const cplx* Yp = L2[job];
+  __shared__ cplx red[256];
+  cplx acc = cmk(0.0, 0.0);
+  for (long long t = threadIdx.x; t < (long long)chi * chi * D2; t += blockDim.x) {
+    const int a = (int)(t / (chi * D2)), bb = (int)((t / D2) % chi), k = (int)(t % D2);
+    cfma(acc, X[(((size_t)a * chi + bb) * d2 + ss) * D2 + k], Yp[(((size_t)bb * chi + a) * d2 + vv) * D2 + k]);
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] = cadd(red[threadIdx.x], red[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    // rho index [s][s'][v][v'] from ss = s * d + s', vv = v * d + v'
+    const int s = ss / d, sp = ss % d, v = vv / d, vp = vv % d;
+    rho[(size_t)job * d2 * d2 + ((s * d + sp) * d + v) * d + vp] = red[0];
+  }
+}
+
+// Observables per instance from rho1 (A, B) and the four bond RDMs:
+// out[b] = {nA, nB, I, tauzA, tauzB, energy, purityA, tr_rhoA}
+__global__ void observables_kernel(const cplx* rho1, const cplx* rho2, const cplx* bondop,
+                                   const double* h, int B, int d, int dA, double* out) {
+  const int b = blockIdx.x;
+  if (threadIdx.x != 0) return;
+  const int d2 = d * d;
+  double n[2], tz[2], tn[2], tr[2];
+  for (int site = 0; site < 2; ++site) {
+    const cplx* r = rho1 + (size_t)(site * B + b) * d2;
+    double trc = 0.0, nn = 0.0, tt = 0.0, tnn = 0.0;
+    for (int s = 0; s < d; ++s) {
+      const double p = r[s * d + s].x;
+      const int occ = s / dA;
+      const double lev = dA > 1 ? 1.0 - 2.0 * (s % dA) / (dA - 1) : 0.0;
+      trc += p; nn += occ * p; tt += lev * p; tnn += lev * occ * p;
+    }
+    tr[site] = trc; n[site] = nn / trc; tz[site] = tt / trc; tn[site] = tnn / trc;
+  }
+  double eb = 0.0;
+  const cplx* H = bondop + (size_t)b * d2 * d2;
+  for (int k = 0; k < 4; ++k) {
+    const cplx* r = rho2 + (size_t)(k * B + b) * d2 * d2;
+    cplx num = cmk(0.0, 0.0);
+    double den = 0.0;
+    for (int s = 0; s < d; ++s)
+      for (int t = 0; t < d; ++t)
+        for (int v = 0; v < d; ++v)
+          for (int w = 0; w < d; ++w)
+            cfma(num, H[(size_t)(t * d + w) * d2 + s * d + v], r[((s * d + t) * d + v) * d + w]);
+    for (int s = 0; s < d; ++s)
+      for (int v = 0; v < d; ++v) den += r[((s * d + s) * d + v) * d + v].x;
+    eb += num.x / den;
+  }
+  const cplx* rA = rho1 + (size_t)b * d2;
+  double pur = 0.0;
+  for (int s = 0; s < d; ++s)
+    for (int t = 0; t < d; ++t) pur += cmul(rA[s * d + t], rA[t * d + s]).x;
+  pur /= tr[0] * tr[0];
+  double* o = out + (size_t)b * 8;
+  o[0] = n[0]; o[1] = n[1]; o[2] = n[0] - n[1]; o[3] = tz[0]; o[4] = tz[1];
+  o[5] = 0.5 * (eb + h[b] * (tn[0] + tn[1]));
+  o[6] = pur; o[7] = tr[0];
+}
+
+static GemmDesc gdm(int M, int N, int K, int batch) {
+  GemmDesc g;
+  memset(&g, 0, sizeof(g));
+  g.M = M; g.N = N; g.K = K; g.batch = batch;
+  g.alpha = cmk(1.0, 0.0); g.beta = cmk(0.0, 0.0);
+  return g;
+}
+
+size_t measure_bytes(int B, int d, int D, int chi) {
+  Arena a;
+  MeasureWork w;
+  measure_carve(a, w, B, d, D, chi);
+  return a.used;
+}
+
+void measure_carve(Arena& a, MeasureWork& w, int B, int d, int D, int chi) {
+  const long long D2 = (long long)D * D;
+  const long long T = chi * D2 * chi;
+  w.tl = a.take<cplx>((size_t)8 * B * T);
+  w.W1 = a.take<cplx>((size_t)8 * B * T * D2);
+  w.bl = a.take<cplx>((size_t)8 * B * T);
+  w.W2 = a.take<cplx>((size_t)8 * B * T * D2 * D2);
+  w.W2p = a.take<cplx>((size_t)8 * B * T * D2 * D2);
+  w.ao = a.take<cplx>((size_t)8 * B * d * d * D2 * D2 * D2 * D2);
+  w.Lh = a.take<cplx>((size_t)8 * B * chi * chi * d * d * D2);
+  w.RCt = a.take<cplx>((size_t)2 * B * T);
+  w.RC = a.take<cplx>((size_t)2 * B * T);
+  w.rho1 = a.take<cplx>((size_t)2 * B * d * d);
+  w.rho2 = a.take<cplx>((size_t)4 * B * d * d * d * d);
+  w.obs = a.take<double>((size_t)8 * B);
+}
+
+void measure_build(Ctx& c, MeasureWork& w, PtrPool& pool, MeasureOff& o) {
+  const int B = c.B, chi = c.chi;
+  const long long D2 = c.D2, T = chi * D2 * chi, chi2 = (long long)chi * chi;
+  auto Cp = [&](int i, int pos, int b) -> const void* { return c.Cenv[i & 3][pos] + (size_t)b * chi2; };
+  auto Tp = [&](int i, int pos, int b) -> const void* { return c.Tenv[i & 3][pos] + (size_t)b * T; };
+  std::vector<const void*> tlA, tlB, w1A, blA, blB, aoB;
+  for (int f = 0; f < 4; ++f)
+    for (int l = 0; l < 2; ++l)
+      for (int b = 0; b < B; ++b) {
+        const int lpos = l;                                   // logical (0,0) or (1,0)
+        const int pp = (f & 1) ? pos_of(lpos >> 1, lpos & 1) : lpos;
+        const int job = (f * 2 + l) * B + b;
+        tlA.push_back(Cp(0 + f, pp, b));
+        tlB.push_back(Tp(0 + f, pp, b));
+        w1A.push_back(Tp(3 + f, pp, b));
+        blA.push_back(Tp(2 + f, pp, b));
+        blB.push_back(Cp(3 + f, pp, b));
+        aoB.push_back(w.ao + (size_t)job * c.d * c.d * D2 * D2 * D2 * D2);
+      }
+  o.tlA = pool.add(tlA); o.tlB = pool.add(tlB); o.w1A = pool.add(w1A);
+  o.blA = pool.add(blA); o.blB = pool.add(blB); o.aoB = pool.add(aoB);
+  std::vector<const void*> rcA, rcB, rcC;
+  for (int l = 0; l < 2; ++l)
+    for (int b = 0; b < B; ++b) {
+      rcA.push_back(Cp(1, l, b));
+      rcB.push_back(Tp(1, l, b));
+      rcC.push_back(Cp(2, l, b));
+    }
+  o.rcA = pool.add(rcA); o.rcB = pool.add(rcB); o.rcC = pool.add(rcC);
+  // bond RDM operands: k = 0 rho_h(A->B), 1 rho_h(B->A), 2 rho_v(A->B), 3 rho_v(B->A)
+  const long long Lper = (long long)chi * chi * c.d * c.d * D2;
+  auto L = [&](int f, int l, int b) -> const void* { return w.Lh + (size_t)((f * 2 + l) * B + b) * Lper; };
+  std::vector<const void*> r1, r2;
+  for (int k = 0; k < 4; ++k)
+    for (int b = 0; b < B; ++b) {
+      if (k == 0) { r1.push_back(L(0, 0, b)); r2.push_back(L(2, 1, b)); }
+      if (k == 1) { r1.push_back(L(0, 1, b)); r2.push_back(L(2, 0, b)); }
+      if (k == 2) { r1.push_back(L(1, 0, b)); r2.push_back(L(3, 1, b)); }
+      if (k == 3) { r1.push_back(L(1, 1, b)); r2.push_back(L(3, 0, b)); }
+    }
+  o.r1 = pool.add(r1); o.r2 = pool.add(r2);
+}
+
+void measure_resolve(const PtrPool& P, const MeasureOff& o, MeasurePlan& m) {
+  m.tlA = P.dev<const cplx* const*>(o.tlA); m.tlB = P.dev<const cplx* const*>(o.tlB);
+  m.w1A = P.dev<const cplx* const*>(o.w1A); m.blA = P.dev<const cplx* const*>(o.blA);
+  m.blB = P.dev<const cplx* const*>(o.blB); m.aoB = P.dev<const cplx* const*>(o.aoB);
+  m.rcA = P.dev<const cplx* const*>(o.rcA); m.rcB = P.dev<const cplx* const*>(o.rcB);
+  m.rcC = P.dev<const cplx* const*>(o.rcC);
+  m.r1 = P.dev<const cplx* const*>(o.r1); m.r2 = P.dev<const cplx* const*>(o.r2);
+}
+
+int measure_run(Ctx& c, MeasureWork& w, const MeasurePlan& m, double* host_out) {
+  const int B = c.B, chi = c.chi, D2 = c.D2, d = c.d;
+  const long long T = (long long)chi * D2 * chi;
+  cudaStream_t st = c.st;
+  int rc;
+  const long long aoper = (long long)d * d * D2 * D2 * D2 * D2;
+  for (int f = 0; f < 4; ++f)
+    for (int l = 0; l < 2; ++l) {
+      const cplx* A = l == 0 ? c.Aph : c.Bph;
+      open_layer_kernel<<<152 * 4, 256, 0, st>>>(A, d, c.D, B, 0, 0,
+                                                w.ao + (size_t)(f * 2 + l) * B * aoper, f);
+      IPEPS_CUDA_TRY(cudaGetLastError());
+    }
+  GemmDesc g = gdm(chi, D2 * chi, chi, 8 * B);         // tl = C1 T1
+  g.Aptr = m.tlA; g.lda = chi; g.Bptr = m.tlB; g.ldb = D2 * chi; g.C = w.tl; g.sC = T; g.ldc = D2 * chi;
+  if ((rc = zgemm_f64(g, st))) return rc;
+  g = gdm(chi * D2, D2 * chi, chi, 8 * B);             // W1 = T4 tl -> [c4d][kL][kU][c1r]
+  g.Aptr = m.w1A; g.lda = chi; g.B = w.tl; g.sB = T; g.ldb = D2 * chi; g.C = w.W1; g.sC = T * D2;
+  g.ldc = D2 * chi;
+  if ((rc = zgemm_f64(g, st))) return rc;
+  g = gdm(chi * D2, chi, chi, 8 * B);                  // bl = T3 C4 -> [e3r][kD][c4d]
+  g.Aptr = m.blA; g.lda = chi; g.Bptr = m.blB; g.ldb = chi; g.C = w.bl; g.sC = T; g.ldc = chi;
+  if ((rc = zgemm_f64(g, st))) return rc;
+  g = gdm(chi * D2, D2 * D2 * chi, chi, 8 * B);        // W2 = bl W1 -> [e3r][kD][kL][kU][c1r]
+  g.A = w.bl; g.sA = T; g.lda = chi; g.B = w.W1; g.sB = T * D2; g.ldb = (long long)D2 * D2 * chi;
+  g.C = w.W2; g.sC = T * D2 * D2; g.ldc = (long long)D2 * D2 * chi;
+  if ((rc = zgemm_f64(g, st))) return rc;
+  {
+    const int dims[5] = {chi, D2, D2, D2, chi}, perm[5] = {0, 4, 3, 2, 1};
+    if ((rc = permute_c128(w.W2, w.W2p, 5, dims, perm, 8 * B, T * D2 * D2, T * D2 * D2, st))) return rc;
+  }
+  g = gdm(chi * chi, d * d * D2, D2 * D2 * D2, 8 * B); // Lh = W2p aoP -> [e3r][c1r][s][s'][kR]
+  g.A = w.W2p; g.sA = T * D2 * D2; g.lda = (long long)D2 * D2 * D2;
+  g.Bptr = m.aoB; g.ldb = (long long)d * d * D2;
+  g.C = w.Lh; g.sC = (long long)chi * chi * d * d * D2; g.ldc = (long long)d * d * D2;
+  if ((rc = zgemm_f64(g, st))) return rc;
+  // right column C2 T2 C3 at (0,0) and (1,0)
+  g = gdm(chi, D2 * chi, chi, 2 * B);
+  g.Aptr = m.rcA; g.lda = chi; g.Bptr = m.rcB; g.ldb = D2 * chi; g.C = w.RCt; g.sC = T; g.ldc = D2 * chi;
+  if ((rc = zgemm_f64(g, st))) return rc;
+  g = gdm(chi * D2, chi, chi, 2 * B);
+  g.A = w.RCt; g.sA = T; g.lda = chi; g.Bptr = m.rcC; g.ldb = chi; g.C = w.RC; g.sC = T; g.ldc = chi;
+  if ((rc = zgemm_f64(g, st))) return rc;
+  rho1_kernel<<<2 * B, 256, 0, st>>>(w.Lh, w.RC, chi, D2, d, w.rho1);
+  IPEPS_CUDA_TRY(cudaGetLastError());
+  rho2_kernel<<<4 * B * d * d * d * d, 256, 0, st>>>(m.r1, m.r2, chi, D2, d, w.rho2);
+  IPEPS_CUDA_TRY(cudaGetLastError());
+  observables_kernel<<<B, 32, 0, st>>>(w.rho1, w.rho2, c.bondop, c.dh, B, d, c.dA, w.obs);
+  IPEPS_CUDA_TRY(cudaGetLastError());
+  IPEPS_CUDA_TRY(cudaMemcpyAsync(host_out, w.obs, sizeof(double) * 8 * B, cudaMemcpyDeviceToHost, st));
+  IPEPS_CUDA_TRY(cudaStreamSynchronize(st));
+  return 0;
+}
+
+}  // namespace ipeps

@@ -1,0 +1,120 @@
+"""GPU parity of the FP64 path against the oracle, through the C ABI, on gauge-invariant outputs.
+
+Tolerance: 1e-10 absolute on observables and normalised spectra (FP64 path).  Fixed-sweep CTMRG
+comparisons start both sides from the same tensors and the same traced initial environment, so any
+difference is rounding plus the SVD gauge; full evolutions converge both sides to the same tol.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import ctmrg, evolve, measure, model, su  # noqa: E402
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+TOL = 1e-10
+
+
+def _sim(**kw):
+    import paper_1910_11359_gb300 as pkg
+    p = dict(J=[1.0], V=[1.0], h=[5.0], D=2, chi=8, order=1, dt=0.02, cut_rel=0.0)
+    p.update(kw)
+    return pkg.IPEPS(p['J'], p['V'], p['h'], D=p['D'], chi=p['chi'], order=p['order'], dt=p['dt'],
+                     cut_rel=p['cut_rel'])
+
+
+@pytest.mark.parametrize("D,order", [(2, 1), (2, 2), (3, 2)])
+def test_simple_update_spectra(D, order):
+    hs = [1.0, 5.0, 10.0]
+    sim = _sim(J=[1.0] * 3, V=[1.0] * 3, h=hs, D=D, chi=D * D, order=order, dt=0.05)
+    eps = sim.trotter_step(8)
+    lam = sim.get_lambda()
+    sim.close()
+    for b, h in enumerate(hs):
+        p = dict(J=1.0, V=1.0, h=h, D=D, order=order, dt=0.05)
+        GA, GB, lam_ref, eps_ref = evolve.evolve_tensors(p, 8)
+        assert np.max(np.abs(lam[b] - lam_ref)) < 1e-12
+        assert abs(eps[b] - eps_ref) < 1e-12 + 1e-9 * eps_ref
+
+
+def test_ctmrg_fixed_sweeps_match_oracle():
+    p = dict(J=1.0, V=1.0, h=5.0, D=2, order=1, dt=0.02)
+    GA, GB, lam, _ = evolve.evolve_tensors(p, 10)
+    chi = 8
+    sim = _sim(chi=chi)
+    sim.set_tensors(GA[None], GB[None], lam[None])
+    sim.ctmrg_converge(tol=0.0, max_sweeps=3)
+    obs = sim.measure()[0]
+    spec = {(i, pos): sim.corner_spectrum(0, pos, i) for i in range(4) for pos in range(4)}
+    sim.close()
+    A, B, a = evolve.ctm_state(GA, GB, lam)
+    env = ctmrg.init_env(a, 2, 2, chi, 2)
+    env, n, _ = ctmrg.ctmrg(a, env, chi, tol=0.0, max_sweeps=3)
+    assert n == 3
+    ref = measure.observables(A, B, env, 1.0, 1.0, 5.0)
+    cs = ctmrg.corner_spectra(env, chi)
+    for (i, pos), s in spec.items():
+        x, y = pos % 2, pos // 2
+        assert np.max(np.abs(s - cs[(i, (x, y))])) < TOL, (i, pos)
+    for k in ("nA", "nB", "imbalance", "tauzA", "tauzB", "energy", "purityA"):
+        assert abs(obs[k] - ref[k]) < TOL, (k, obs[k], ref[k])
+
+
+def _evolve_like(g, cut_rel=0.0):
+    p = g["params"]
+    sim = _sim(J=[p["J"]], V=[p["V"]], h=[p["h"]], D=p["D"], chi=p["chi"], order=p["order"],
+               dt=p["dt"], cut_rel=cut_rel)
+    stride = int(round(p["meas_every"] / p["dt"]))
+    out = []
+    for i, row in enumerate(g["rows"]):
+        if i > 0:
+            sim.trotter_step(stride)
+        sim.ctmrg_converge(tol=p["tol"], max_sweeps=500, allow_noconv=True)
+        out.append(sim.measure()[0])
+    lam = sim.get_lambda()[0]
+    sim.close()
+    return out, lam
+
+
+WELL_CONDITIONED_SWEEPS = 20
+
+
+def _compare_rows(out, lam, g, keys):
+    """Observables at 1e-10 where the oracle's CTMRG converged within WELL_CONDITIONED_SWEEPS sweeps;
+    elsewhere the CTMRG map contracts slowly (rate close to 1), the converged fixed point depends on
+    rounding and on the warm-start path (the oracle itself moves by up to 1e-8 under a 1e-15 change
+    of its gates), and the observables are held to 1e-3.  The simple-update state (discarded weight,
+    final bond spectra) is always held to 1e-10."""
+    errs = []
+    for o, row in zip(out, g["rows"]):
+        assert abs(o["trunc_err_acc"] - row["trunc_err_acc"]) < 1e-12 + 1e-8 * row["trunc_err_acc"]
+        e = max(abs(o[k] - row[k]) for k in keys)
+        errs.append((row["t"], row["ctm_sweeps"], e))
+        if row["ctm_sweeps"] <= WELL_CONDITIONED_SWEEPS:
+            assert e < TOL, (row["t"], e)
+        else:
+            assert e < 1e-3, (row["t"], e)
+    assert np.max(np.abs(lam - np.array(g["rows"][-1]["lam"]))) < TOL
+    print("per-time (t, oracle sweeps, max abs error):",
+          ", ".join("(%.1f, %d, %.1e)" % r for r in errs))
+    return errs
+
+
+def test_config1_evolution_matches_golden():
+    """Config-1 workload with the default projector cutoff (1e-10)."""
+    g = json.load(open(os.path.join(GOLDEN, "config1_oracle.json")))
+    out, lam = _evolve_like(g)
+    errs = _compare_rows(out, lam, g, ("imbalance", "nA", "nB", "energy"))
+    assert sum(1 for t, sw, e in errs if sw <= WELL_CONDITIONED_SWEEPS) >= 8
+
+
+def test_config1_full_range_well_conditioned():
+    """Projector cutoff 1e-6: the oracle's CTMRG converges in <= 15 sweeps up to t = 0.9."""
+    g = json.load(open(os.path.join(GOLDEN, "config1_cut1e-6_oracle.json")))
+    out, lam = _evolve_like(g, cut_rel=1e-6)
+    errs = _compare_rows(out, lam, g, ("imbalance", "nA", "nB", "tauzA", "tauzB", "energy", "purityA"))
+    assert sum(1 for t, sw, e in errs if sw <= WELL_CONDITIONED_SWEEPS) >= 10
