@@ -1,0 +1,295 @@
+#!/usr/bin/env python
+"""Benchmark of the iPEPS real-time-evolution hot path: Trotter + CTMRG steps per second.
+
+Workload (one GPU): three instances of the dilated hard-core boson lattice (J = V = 1,
+h = 1, 5, 10), PEPS bond dimension D = 3, environment chi = 18, second-order Trotter steps of
+dt = 0.05 with the CTMRG environment converged to 1e-10 and the observables read out every 0.25
+(every 5 Trotter steps).  One bench step is one such readout interval for all three instances:
+5 Trotter steps (7 bond updates each), CTMRG to convergence, measurement.
+
+metric  Trotter steps per second, summed over instances (and ranks), CTMRG and readout included
+value   device-resident state, timed with CUDA events on the library's stream
+e2e     the same steps through the public API with the state copied in from pinned host memory
+        (ipeps_set_tensors) and the tensors and observables copied back every step
+roofline  the kernel class with the largest share of the timed region, algorithmic flops per
+          launch over its event-timed average duration, against the FP64 rate measured in this run
+cpu_baseline  the FP64 oracle on the host, one instance, a bounded sample of the same workload
+
+--impl reference times the oracle (this workload's reference implementation) instead.
+Multi-GPU (torchrun): independent replicas, one per rank, no collectives on the data path.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+J, V, HS = 1.0, 1.0, (1.0, 5.0, 10.0)
+D, CHI, ORDER, DT = 3, 18, 2, 0.05
+STEPS_PER_READOUT = 5          # 0.25 / 0.05
+TOL, MAX_SWEEPS = 1e-10, 500
+METRIC = "Trotter+CTMRG steps/s"
+UNIT = "Trotter steps/s"
+WORKLOAD = ("iPEPS MBL quench, D=3 chi=18, 3 instances (J=V=1, h=1,5,10), 2nd-order dt=0.05, "
+            "CTMRG to 1e-10 + readout every 0.25")
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=6)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("native", "reference"), default="native")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- clocks sampler
+class Clocks:
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._proc = None
+
+    def start(self):
+        cmd = ["nvidia-smi", "-i", str(self.index), "--query-gpu=clocks.sm,clocks.max.sm,power.draw,"
+               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+               "--format=csv,noheader,nounits", "-lms", "200"]
+        try:
+            self._proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                          text=True)
+        except OSError:
+            self._proc = None
+            return
+        threading.Thread(target=self._read, daemon=True).start()
+
+    def _read(self):
+        for line in self._proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self._proc is not None:
+            self._proc.terminate()
+            try:
+                self._proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self._proc.kill()
+        time.sleep(0.1)
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[3 + i] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(self.samples)}
+
+
+# ----------------------------------------------------------------------------- oracle sample
+ORACLE_SAMPLE = ("one instance (h=5), 5 second-order Trotter steps from t=0, 2 CTMRG sweeps from "
+                 "the traced start and one readout; scaled to a full step with the GPU run's mean "
+                 "sweeps per readout")
+
+
+def oracle_sample(sweeps_per_readout):
+    """Time the oracle on a bounded sample; returns (steps/s, sample seconds)."""
+    code = r"""
+import json, sys, time
+sys.path.insert(0, %r)
+from oracle import ctmrg, evolve, measure
+p = dict(J=1.0, V=1.0, h=5.0, D=3, chi=18, order=2, dt=0.05)
+t0 = time.perf_counter(); GA, GB, lam, _ = evolve.evolve_tensors(p, 5); t1 = time.perf_counter()
+A, B, a = evolve.ctm_state(GA, GB, lam)
+env = ctmrg.init_env(a, 2, 2, 18, 3)
+t2 = time.perf_counter()
+for _ in range(2):
+    env = ctmrg.sweep(a, env, 18)
+t3 = time.perf_counter()
+measure.observables(A, B, env, 1.0, 1.0, 5.0)
+t4 = time.perf_counter()
+print(json.dumps(dict(su=t1 - t0, sweep=(t3 - t2) / 2, measure=t4 - t3, total=t4 - t0)))
+""" % ROOT
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                         timeout=600)
+    r = json.loads(out.stdout.strip().splitlines()[-1])
+    per_instance = r["su"] + sweeps_per_readout * r["sweep"] + r["measure"]
+    rate = STEPS_PER_READOUT / per_instance          # Trotter steps/s for one instance, one core
+    return rate, r["total"], r
+
+
+def reference_main(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    mean_sweeps = 10.0
+    times = []
+    samples = []
+    for i in range(args.warmup + args.steps):
+        rate, sec, r = oracle_sample(mean_sweeps)
+        if i >= args.warmup:
+            times.append(STEPS_PER_READOUT / rate * len(HS))
+            samples.append(rate)
+    value = len(HS) * STEPS_PER_READOUT * len(times) / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "l2": "host run"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": ORACLE_SAMPLE + "; %.0f sweeps per readout assumed" % mean_sweeps},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ----------------------------------------------------------------------------- native arm
+def native_main(args):
+    import torch
+    import paper_1910_11359_gb300 as pkg
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    B = len(HS)
+    sim = pkg.IPEPS([J] * B, [V] * B, list(HS), D=D, chi=CHI, order=ORDER, dt=DT,
+                    stream=stream.cuda_stream)
+
+    def step():
+        sim.trotter_step(STEPS_PER_READOUT, sync=False)
+        sw, dl, rc = sim.ctmrg_converge(tol=TOL, max_sweeps=MAX_SWEEPS, allow_noconv=True)
+        return sim.measure(), sw
+
+    with torch.cuda.stream(stream):
+        sim.ctmrg_converge(tol=TOL, max_sweeps=MAX_SWEEPS, allow_noconv=True)
+        sim.measure()
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        clocks = Clocks(local)
+        clocks.start()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        launches0 = pkg.launch_count()
+        pkg.profile_enable(True)
+        total_ms = 0.0
+        sweeps = []
+        last = None
+        for _ in range(args.steps):
+            flush.fill_(1.0)                                  # L2 flush between timed steps
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            last, sw = step()
+            e1.record(stream)
+            e1.synchronize()
+            total_ms += e0.elapsed_time(e1)
+            sweeps.extend(int(s) for s in sw)
+        torch.cuda.synchronize()
+        prof = pkg.profile_read()
+        pkg.profile_enable(False)
+        launches = pkg.launch_count() - launches0
+        if dist is not None:
+            t = torch.tensor([total_ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_ms = float(t.item())
+            dist.barrier()
+        clk = clocks.stop()
+        steps_done = B * STEPS_PER_READOUT * args.steps * world
+        value = steps_done / (total_ms * 1e-3)
+
+        # end to end through the public API with host buffers (pinned), copies inside the timing
+        GA, GB = sim.get_tensors()
+        lam = sim.get_lambda()
+        hGA = torch.from_numpy(GA.view(np.float64)).pin_memory().numpy().view(np.complex128)
+        hGB = torch.from_numpy(GB.view(np.float64)).pin_memory().numpy().view(np.complex128)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            sim.set_tensors(hGA, hGB, lam)
+            obs, _ = step()
+            gA, gB = sim.get_tensors()
+            hGA[...] = gA
+            hGB[...] = gB
+            lam = sim.get_lambda()
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        e2e_value = B * STEPS_PER_READOUT * args.e2e_steps * world / e2e_s
+        h2d = 2 * GA.nbytes + lam.nbytes
+        d2h = 2 * GA.nbytes + lam.nbytes + B * 88
+    sim.close()
+
+    # roofline of the dominant kernel class
+    dom = max(prof.items(), key=lambda kv: kv[1][0])
+    name, (ms, flops, n) = dom
+    peak = pkg.fp64_peak_tflops()
+    achieved = flops / (ms * 1e-3) / 1e12 if ms > 0 else 0.0
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tfile):
+        tj = json.load(open(tfile))
+        if tj.get("kernel") == name and tj.get("workload") == WORKLOAD:
+            traffic = tj.get("dram_bytes_per_launch")
+    shares = {k: round(v[0] / total_ms, 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])
+              if v[0] > 0}
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+    mean_sweeps = float(np.mean(sweeps)) if sweeps else 10.0
+    cpu_rate, cpu_sec, cpu_parts = oracle_sample(mean_sweeps)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "instances_per_gpu": B, "D": D, "chi": CHI,
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "flushed (256 MiB write) between timed steps",
+                   "mean_ctm_sweeps_per_readout": mean_sweeps},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "roofline": {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak if peak else None,
+                     "traffic": traffic, "launches": n, "avg_launch_us": 1e3 * ms / max(n, 1),
+                     "peak_source": "FP64 FMA rate measured in this run (no FP64 tensor path)"},
+        "kernel_time_share": shares,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "cpu_baseline": {"value": cpu_rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": ORACLE_SAMPLE, "sample_seconds": round(cpu_sec, 2),
+                         "parts_s": {k: round(v, 3) for k, v in cpu_parts.items()}},
+    }
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_main(args)
+    return native_main(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

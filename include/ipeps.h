@@ -55,6 +55,8 @@ typedef struct {
   double ctm_cut_rel;       /* CTMRG projector truncation: singular values of the product of the two
                                half-systems below ctm_cut_rel times the largest are dropped
                                (<= 0 selects 1e-10) */
+  int projector_svd;        /* 0 = automatic, 1 = full Jacobi SVD of the chi D^2 x chi D^2 product,
+                               2 = top-(chi+8) subspace iteration */
 } ipeps_params;
 
 typedef struct {

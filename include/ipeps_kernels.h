@@ -37,6 +37,21 @@ int ipeps_kernel_permute(const double* in, double* out, int rank, const int* dim
 int ipeps_kernel_svd(int m, int n, int batch, const double* A, double* U, double* S, double* V,
                      double tol, int max_sweeps, int* sweeps_out, void* stream);
 
+/* Launch accounting (all handles, all threads).  ipeps_launch_count: kernels launched by the
+ * library since it was loaded.  ipeps_profile_enable(1) resets and starts per-class timing: every
+ * launch is then bracketed by CUDA events recorded on the stream it is launched on (this adds a
+ * little host overhead); ipeps_profile_read synchronises the device and fills, per kernel class
+ * (ipeps_profile_classes() entries, names from ipeps_profile_name), the summed event time in ms,
+ * the summed algorithmic FP64 flops and the number of launches.  Arrays may be NULL. */
+unsigned long long ipeps_launch_count(void);
+/* Measured FP64 FMA throughput of the current device in TFLOP/s (independent FMA chains on every
+ * SM; best of three timed launches).  Allocates a small scratch buffer. */
+int ipeps_kernel_fp64_peak(double* tflops_out);
+int ipeps_profile_enable(int on);
+int ipeps_profile_classes(void);
+const char* ipeps_profile_name(int k);
+int ipeps_profile_read(double* ms, double* flops, unsigned long long* launches);
+
 #ifdef __cplusplus
 }
 #endif

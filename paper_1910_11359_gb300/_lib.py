@@ -28,7 +28,8 @@ class Params(ctypes.Structure):
                 ("chi", ctypes.c_int), ("trotter_order", ctypes.c_int), ("dt", ctypes.c_double),
                 ("precision", ctypes.c_int), ("seed", ctypes.c_ulonglong),
                 ("J", ctypes.POINTER(ctypes.c_double)), ("V", ctypes.POINTER(ctypes.c_double)),
-                ("h", ctypes.POINTER(ctypes.c_double)), ("ctm_cut_rel", ctypes.c_double)]
+                ("h", ctypes.POINTER(ctypes.c_double)), ("ctm_cut_rel", ctypes.c_double),
+                ("projector_svd", ctypes.c_int)]
 
 
 class Obs(ctypes.Structure):
@@ -43,7 +44,9 @@ _lib = None
 EXPORTS = ["ipeps_init", "ipeps_set_tensors", "ipeps_trotter_step", "ctmrg_converge", "ctmrg_reset",
            "ipeps_measure", "ipeps_corner_spectrum", "ipeps_get_lambda", "ipeps_get_tensors",
            "ipeps_footprint_bytes", "ipeps_destroy", "ipeps_last_error", "ipeps_kernel_zgemm",
-           "ipeps_kernel_permute", "ipeps_kernel_svd", "ipeps_kernel_gate"]
+           "ipeps_kernel_permute", "ipeps_kernel_svd", "ipeps_kernel_gate", "ipeps_launch_count",
+           "ipeps_profile_enable", "ipeps_profile_classes", "ipeps_profile_name", "ipeps_profile_read",
+           "ipeps_kernel_fp64_peak"]
 
 
 def lib():
@@ -74,8 +77,16 @@ def lib():
     L.ipeps_kernel_permute.argtypes = [vp, vp, i, ip, ip, i, ll, ll, vp]
     L.ipeps_kernel_svd.argtypes = [i, i, i, vp, vp, vp, vp, d, i, vp, vp]
     L.ipeps_kernel_gate.argtypes = [d, d, d, d, dp]
+    L.ipeps_launch_count.argtypes = []
+    L.ipeps_launch_count.restype = ctypes.c_ulonglong
+    L.ipeps_profile_enable.argtypes = [i]
+    L.ipeps_profile_classes.argtypes = []
+    L.ipeps_profile_name.argtypes = [i]
+    L.ipeps_profile_name.restype = ctypes.c_char_p
+    L.ipeps_profile_read.argtypes = [dp, dp, P(ctypes.c_ulonglong)]
+    L.ipeps_kernel_fp64_peak.argtypes = [dp]
     for name in EXPORTS:
-        if name not in ("ipeps_last_error",):
+        if name not in ("ipeps_last_error", "ipeps_launch_count", "ipeps_profile_name"):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -92,12 +103,13 @@ def _check(rc, handle=None, allow=()):
     return rc
 
 
-def _params(J, V, h, D, chi, order, dt, precision, seed, cut_rel=0.0):
+def _params(J, V, h, D, chi, order, dt, precision, seed, cut_rel=0.0, projector_svd=0):
     J = np.ascontiguousarray(np.atleast_1d(J), dtype=np.float64)
     V = np.ascontiguousarray(np.broadcast_to(np.atleast_1d(V), J.shape), dtype=np.float64)
     h = np.ascontiguousarray(np.broadcast_to(np.atleast_1d(h), J.shape), dtype=np.float64)
     p = Params(batch=len(J), d_A=2, D=D, chi=chi, trotter_order=order, dt=dt, precision=precision,
-               seed=seed, J=_dptr(J), V=_dptr(V), h=_dptr(h), ctm_cut_rel=cut_rel)
+               seed=seed, J=_dptr(J), V=_dptr(V), h=_dptr(h), ctm_cut_rel=cut_rel,
+               projector_svd=projector_svd)
     return p, (J, V, h)
 
 
@@ -112,8 +124,8 @@ class IPEPS:
     """One library handle: ``batch`` = len(J) instances with shared D, chi, Trotter order and dt."""
 
     def __init__(self, J, V, h, D, chi, order=1, dt=0.02, precision=FP64, seed=0, stream=None,
-                 cut_rel=0.0):
-        p, self._keep = _params(J, V, h, D, chi, order, dt, precision, seed, cut_rel)
+                 cut_rel=0.0, projector_svd=0):
+        p, self._keep = _params(J, V, h, D, chi, order, dt, precision, seed, cut_rel, projector_svd)
         self.batch, self.D, self.chi, self.d = p.batch, D, chi, 4
         self._h = ctypes.c_void_p(None)
         st = ctypes.c_void_p(stream) if stream else None
@@ -179,3 +191,28 @@ class IPEPS:
         _check(lib().ipeps_get_tensors(self._h, _dptr(GA.view(np.float64)),
                                        _dptr(GB.view(np.float64))), self._h)
         return GA, GB
+
+
+def launch_count():
+    """Kernels launched by the library since it was loaded."""
+    return int(lib().ipeps_launch_count())
+
+
+def profile_enable(on=True):
+    _check(lib().ipeps_profile_enable(1 if on else 0))
+
+
+def profile_read():
+    """Per kernel class: {name: (ms, flops, launches)} accumulated since profile_enable(True)."""
+    L = lib()
+    n = L.ipeps_profile_classes()
+    ms, fl = np.zeros(n), np.zeros(n)
+    cnt = np.zeros(n, dtype=np.uint64)
+    _check(L.ipeps_profile_read(_dptr(ms), _dptr(fl), cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_ulonglong))))
+    return {L.ipeps_profile_name(k).decode(): (float(ms[k]), float(fl[k]), int(cnt[k])) for k in range(n)}
+
+
+def fp64_peak_tflops():
+    out = ctypes.c_double(0.0)
+    _check(lib().ipeps_kernel_fp64_peak(ctypes.byref(out)))
+    return out.value

@@ -64,7 +64,11 @@ ipeps_status validate(const ipeps_params* p, std::string* why) {
   if (p->precision != IPEPS_FP64) { *why = "this build implements precision = IPEPS_FP64 only"; return IPEPS_EUNSUPPORTED; }
   if (!p->J || !p->V || !p->h) { *why = "J, V, h arrays are required"; return IPEPS_EINVAL; }
   const int N = p->chi * p->D * p->D;
-  if (!jacobi_svd_fits(N, N)) { *why = "chi * D^2 too large for the full-SVD projector path"; return IPEPS_EUNSUPPORTED; }
+  const int k = p->chi + 8 < N ? p->chi + 8 : N;
+  const bool sub = p->projector_svd == 2 ? k < N : (p->projector_svd == 1 ? false : N > 2 * k);
+  if (p->projector_svd < 0 || p->projector_svd > 2) { *why = "projector_svd must be 0, 1 or 2"; return IPEPS_EINVAL; }
+  if (sub && k > 256) { *why = "chi + 8 must not exceed 256 for the subspace projector SVD"; return IPEPS_EUNSUPPORTED; }
+  if (!jacobi_svd_fits(N, sub ? k : N)) { *why = "chi * D^2 too large for the projector SVD"; return IPEPS_EUNSUPPORTED; }
   return IPEPS_OK;
 }
 
@@ -136,6 +140,8 @@ void set_params(Ctx& c, const ipeps_params* p) {
   c.N = c.chi * c.D2; c.order = p->trotter_order; c.dt = p->dt; c.precision = p->precision;
   c.seed = p->seed;
   c.cut_rel = p->ctm_cut_rel > 0.0 ? p->ctm_cut_rel : 1e-10;
+  c.k = c.chi + 8 < c.N ? c.chi + 8 : c.N;
+  c.subspace = p->projector_svd == 2 ? c.k < c.N : (p->projector_svd == 1 ? false : c.N > 2 * c.k);
 }
 
 }  // namespace
@@ -354,7 +360,7 @@ ipeps_status ipeps_corner_spectrum(ipeps_h h, int inst, int pos, int corner, dou
   SvdDesc sd;
   sd.m = c.chi; sd.n = c.chi; sd.batch = 16 * c.B;
   sd.A = c.w.csA; sd.lda = c.chi; sd.U = nullptr; sd.ldu = 0; sd.S = c.w.csS; sd.V = nullptr; sd.ldv = 0;
-  sd.tol = 4e-16 * c.chi; sd.max_sweeps = 80; sd.err = c.derr; sd.sweeps_out = nullptr;
+  sd.tol = 4e-16 * c.chi; sd.max_sweeps = 80; sd.err = c.derr; sd.sweeps_out = nullptr; sd.skip = nullptr;
   int rc = jacobi_svd(sd, c.st);
   if (rc) return from_rc(h, rc);
   std::vector<double> s(c.chi);
@@ -454,7 +460,7 @@ int ipeps_kernel_svd(int m, int n, int batch, const double* A, double* U, double
   d.U = U ? (cplx* const*)(dp + batch) : nullptr; d.ldu = n;
   d.S = (double* const*)(dp + 2 * batch);
   d.V = V ? (cplx* const*)(dp + 3 * batch) : nullptr; d.ldv = n;
-  d.tol = tol; d.max_sweeps = max_sweeps; d.err = derr; d.sweeps_out = sweeps_out;
+  d.tol = tol; d.max_sweeps = max_sweeps; d.err = derr; d.sweeps_out = sweeps_out; d.skip = nullptr;
   int rc = jacobi_svd(d, st);
   unsigned e = 0;
   if (!rc) {

@@ -27,6 +27,7 @@
 
 #include "ctx.cuh"
 #include "model.cuh"
+#include "prof.cuh"
 
 namespace ipeps {
 
@@ -78,6 +79,18 @@ void ctm_carve(Ctx& c) {
   w.frozen = a.take<int>(B);
   w.sweeps = a.take<int>(B);
   w.have_prev = a.take<int>(1);
+  const long long Nk = (long long)c.N * c.k, kk = (long long)c.k * c.k;
+  w.Vfin = a.take<cplx>((size_t)8 * 2 * B * Nk);
+  w.Vw = a.take<cplx>((size_t)2 * B * Nk);
+  w.Ysub = a.take<cplx>((size_t)2 * B * Nk);
+  w.Uy = a.take<cplx>((size_t)2 * B * Nk);
+  w.W = a.take<cplx>((size_t)2 * B * kk);
+  w.Zsub = a.take<cplx>((size_t)2 * B * Nk);
+  w.Vz = a.take<cplx>((size_t)2 * B * Nk);
+  w.Sy = a.take<double>((size_t)2 * B * c.k);
+  w.Sz = a.take<double>((size_t)2 * B * c.k);
+  w.sub_done = a.take<int>((size_t)2 * B);
+  w.sub_rounds = a.take<int>((size_t)2 * B);
 }
 
 void ctm_build_plans(Ctx& c) {
@@ -160,6 +173,19 @@ void ctm_build_plans(Ctx& c) {
   c.off.csA = pool.add(csA); c.off.csS = pool.add(csS);
   c.off.pA = pool.add(pA); c.off.pU = pool.add(pU); c.off.pS = pool.add(pS); c.off.pV = pool.add(pV);
   c.off.envC = pool.add(envC); c.off.envT = pool.add(envT);
+  const long long Nk = (long long)c.N * c.k, kk = (long long)c.k * c.k;
+  std::vector<const void*> yA, yU, yS, yV, zA, zU, zS;
+  for (int q = 0; q < 2 * B; ++q) {
+    yA.push_back(w.Ysub + (size_t)q * Nk);
+    yU.push_back(w.Uy + (size_t)q * Nk);
+    yS.push_back(w.Sy + (size_t)q * c.k);
+    yV.push_back(w.W + (size_t)q * kk);
+    zA.push_back(w.Zsub + (size_t)q * Nk);
+    zU.push_back(w.Vz + (size_t)q * Nk);
+    zS.push_back(w.Sz + (size_t)q * c.k);
+  }
+  c.off.yA = pool.add(yA); c.off.yU = pool.add(yU); c.off.yS = pool.add(yS); c.off.yV = pool.add(yV);
+  c.off.zA = pool.add(zA); c.off.zU = pool.add(zU); c.off.zS = pool.add(zS);
 }
 
 void ctm_resolve_plans(Ctx& c) {
@@ -191,6 +217,10 @@ void ctm_resolve_plans(Ctx& c) {
   c.w.pV = P.dev<cplx* const*>(c.off.pV);
   c.w.envC = P.dev<cplx* const*>(c.off.envC);
   c.w.envT = P.dev<cplx* const*>(c.off.envT);
+  c.w.yA = P.dev<const cplx* const*>(c.off.yA); c.w.yU = P.dev<cplx* const*>(c.off.yU);
+  c.w.yS = P.dev<double* const*>(c.off.yS); c.w.yV = P.dev<cplx* const*>(c.off.yV);
+  c.w.zA = P.dev<const cplx* const*>(c.off.zA); c.w.zU = P.dev<cplx* const*>(c.off.zU);
+  c.w.zS = P.dev<double* const*>(c.off.zS);
 }
 
 // ----------------------------------------------------------------------------- small kernels
@@ -253,15 +283,17 @@ __global__ void env_init_kernel(const cplx* a0A, const cplx* a0B, int B, int D, 
 
 // Projector factors from the SVD of M: rank K (multiplets at the cut kept whole, values below
 // cut_rel of the largest dropped), Vs = V[:, :K] S^{-1/2}, Us = U[:, :K] S^{-1/2}, zero-padded to chi.
-__global__ void proj_prep_kernel(const double* S, const cplx* U, const cplx* V, int N, int chi,
-                                 long long ldu, long long stride_uv, cplx* Us, cplx* Vs, int* kept,
-                                 double degen_rtol, double tiny_rel, double cut_rel) {
+__global__ void proj_prep_kernel(const double* S, long long s_stride, int ns, const cplx* U,
+                                 const cplx* V, int N, int chi, long long ldu, long long stride_uv,
+                                 cplx* Us, cplx* Vs, int* kept, double degen_rtol, double tiny_rel,
+                                 double cut_rel) {
+  // S: ns singular values (descending) per problem; U, V: N x (>= chi) with leading dimension ldu
   const int q = blockIdx.x;
-  const double* s = S + (size_t)q * N;
+  const double* s = S + (size_t)q * s_stride;
   __shared__ int sK;
   if (threadIdx.x == 0) {
-    int K = chi < N ? chi : N;
-    while (K > 1 && K < N && s[K] > tiny_rel * s[0] && s[K - 1] / s[K] - 1.0 < degen_rtol) --K;
+    int K = chi < ns ? chi : ns;
+    while (K > 1 && K < ns && s[K] > tiny_rel * s[0] && s[K - 1] / s[K] - 1.0 < degen_rtol) --K;
     int cnt = 0;
     for (int j = 0; j < K; ++j) cnt += s[j] > cut_rel * s[0];
     K = cnt < K ? cnt : K;
@@ -285,6 +317,39 @@ __global__ void proj_prep_kernel(const double* S, const cplx* U, const cplx* V, 
     } else {
       Uo[idx] = cmk(0.0, 0.0);
       Vo[idx] = cmk(0.0, 0.0);
+    }
+  }
+}
+
+// counter-based uniform draws in [-1, 1): splitmix64 of (seed, stream, index)
+__device__ __forceinline__ double rand_unit(unsigned long long seed, unsigned long long stream,
+                                            unsigned long long i) {
+  unsigned long long z = seed + 0x9E3779B97F4A7C15ull * (stream * 0x100000001B3ull + i + 1);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+}
+
+// Starting block of the subspace iteration: the slot's previous right vectors, or random columns
+// on the slot's first use.  Columns of `src` whose singular value (sv, may be null) is not above
+// tiny * sv[0] are refilled with random columns so the block keeps full rank.
+__global__ void sub_fill_kernel(const cplx* src, const double* sv, int N, int k, int random_all,
+                                unsigned long long seed, unsigned long long stream, cplx* dst,
+                                const int* skip = nullptr) {
+  const int q = blockIdx.x;
+  if (skip && skip[q]) return;
+  const cplx* sq = src ? src + (size_t)q * N * k : nullptr;
+  const double* s = sv ? sv + (size_t)q * k : nullptr;
+  cplx* dq = dst + (size_t)q * N * k;
+  for (int idx = threadIdx.x; idx < N * k; idx += blockDim.x) {
+    const int j = idx % k;
+    const bool fresh = random_all || (s && !(s[j] > 1e-300 && s[j] > 1e-15 * s[0]));
+    if (fresh) {
+      const unsigned long long id = ((unsigned long long)q * N * k + idx) * 2;
+      dq[idx] = cmk(rand_unit(seed, stream, id), rand_unit(seed, stream, id + 1));
+    } else {
+      dq[idx] = sq[idx];
     }
   }
 }
@@ -355,10 +420,13 @@ int ctm_prepare_tensors(Ctx& c) {
 }
 
 int ctm_init_env(Ctx& c) {
-  env_init_kernel<<<8 * NPOS * c.B, 256, 0, c.st>>>(c.a_rot(0, 0), c.a_rot(1, 0), c.B, c.D, c.chi,
-                                                    c.w.envC, c.w.envT);
+  IPEPS_LAUNCH(K_ENV_INIT, 0, c.st,
+               env_init_kernel<<<8 * NPOS * c.B, 256, 0, c.st>>>(c.a_rot(0, 0), c.a_rot(1, 0), c.B, c.D, c.chi,
+                                                                 c.w.envC, c.w.envT));
   IPEPS_CUDA_TRY(cudaGetLastError());
   c.env_valid = true;
+  for (int f = 0; f < 4; ++f)
+    for (int x = 0; x < 2; ++x) c.slot_warm[f][x] = false;
   return 0;
 }
 
@@ -369,6 +437,132 @@ static GemmDesc gd(int M, int N, int K, int batch) {
   g.opA = OP_N; g.opB = OP_N;
   g.alpha = cmk(1.0, 0.0); g.beta = cmk(0.0, 0.0);
   return g;
+}
+
+// Columns of Z = M^+ U_y with negligible norm (M has rank below k, or u_j is a zero column) are
+// replaced by random columns before Z is orthonormalised, so the block keeps full rank.
+__global__ void sub_refill_kernel(cplx* Z, int N, int k, unsigned long long seed,
+                                  unsigned long long stream, const int* skip) {
+  const int q = blockIdx.x;
+  if (skip[q]) return;
+  cplx* Zq = Z + (size_t)q * N * k;
+  __shared__ double nrm[256];
+  __shared__ double mx;
+  for (int j = threadIdx.x; j < k; j += blockDim.x) {
+    double acc = 0.0;
+    for (int i = 0; i < N; ++i) acc += cabs2(Zq[(size_t)i * k + j]);
+    nrm[j] = sqrt(acc);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int j = 0; j < k; ++j) m = fmax(m, nrm[j]);
+    mx = m;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < N * k; idx += blockDim.x) {
+    const int j = idx % k;
+    if (!(nrm[j] > 1e-300 && nrm[j] > 1e-13 * mx)) {
+      const unsigned long long id = ((unsigned long long)q * N * k + idx) * 2;
+      Zq[idx] = cmk(rand_unit(seed, stream, id), rand_unit(seed, stream, id + 1));
+    }
+  }
+}
+
+// Convergence of the subspace iteration: with Y = M V = U_y S_y W^+ and V_f = V W (so that
+// M v_j = s_j u_j holds by construction), the triplets are converged when M^+ u_j = s_j v_j too:
+// residual_j = || (M^+ U_y)_j - s_j (V_f)_j || <= rtol * s_1 for the first min(k, chi + 1) columns.
+__global__ void sub_residual_kernel(const cplx* Z, const cplx* Vf, const double* S, int N, int k,
+                                    int ncheck, double rtol, int* done, int* rounds) {
+  const int q = blockIdx.x;
+  if (done[q]) return;
+  const cplx* Zq = Z + (size_t)q * N * k;
+  const cplx* Vq = Vf + (size_t)q * N * k;
+  const double* s = S + (size_t)q * k;
+  __shared__ double red[256];
+  double worst = 0.0;
+  for (int j = 0; j < ncheck; ++j) {
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+      const cplx r = csub(Zq[(size_t)i * k + j], cscale(Vq[(size_t)i * k + j], s[j]));
+      acc += cabs2(r);
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) worst = fmax(worst, red[0]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    rounds[q] += 1;
+    if (sqrt(worst) <= rtol * s[0]) done[q] = 1;
+  }
+}
+
+// Top-k SVD of M = R R~ (k = chi + 8 < N/2) by block subspace iteration with Jacobi
+// orthonormalisation.  Each round: Y = M V = U_y S_y W^+ (Jacobi), V_f = V W, Z = M^+ U_y; the
+// triplets (U_y, S_y, V_f) are accepted once Z matches V_f S_y (residual test above); otherwise
+// Z (negligible columns refilled at random) = V_z S_z X^+ (Jacobi), V <- V_z (orthonormal) and the
+// next round follows.  Converged problems are skipped by
+// every later launch.  The iteration starts from the slot's previous right vectors (random on the
+// slot's first use); at most 8 rounds per call (40 on first use) -- the outer CTMRG loop calls again.
+static int subspace_svd(Ctx& c, int f, int x, const cplx* R, const cplx* Rt) {
+  CtmWork& w = c.w;
+  const int B = c.B, N = c.N, k = c.k, chi = c.chi;
+  const long long N2 = c.N2(), Nk = (long long)N * k, kk = (long long)k * k;
+  cudaStream_t st = c.st;
+  int rc;
+  cplx* slot = w.Vfin + (size_t)(f * 2 + x) * 2 * B * Nk;
+  const bool warm = c.slot_warm[f][x];
+  const unsigned long long stream_id = (unsigned long long)(f * 2 + x);
+  IPEPS_CUDA_TRY(cudaMemsetAsync(w.sub_done, 0, sizeof(int) * 2 * B, st));
+  IPEPS_CUDA_TRY(cudaMemsetAsync(w.sub_rounds, 0, sizeof(int) * 2 * B, st));
+  IPEPS_LAUNCH(K_PROJ_PREP, 0, st,
+               sub_fill_kernel<<<2 * B, 256, 0, st>>>(slot, nullptr, N, k, warm ? 0 : 1, c.seed,
+                                                      stream_id, w.Vw));
+  const int rounds = warm ? 8 : 40;
+  SvdDesc yd;
+  yd.m = N; yd.n = k; yd.batch = 2 * B;
+  yd.A = w.yA; yd.lda = k; yd.U = w.yU; yd.ldu = k; yd.S = w.yS; yd.V = w.yV; yd.ldv = k;
+  yd.tol = 4e-16 * N; yd.max_sweeps = 60; yd.err = c.derr; yd.sweeps_out = nullptr;
+  yd.skip = w.sub_done;
+  SvdDesc zd = yd;
+  zd.A = w.zA; zd.U = w.zU; zd.S = w.zS; zd.V = nullptr;
+  const int ncheck = chi + 1 < k ? chi + 1 : k;
+  for (int it = 0; it < rounds; ++it) {
+    GemmDesc g = gd(N, k, N, 2 * B);            // Y = M V
+    g.A = w.M; g.sA = N2; g.lda = N; g.B = w.Vw; g.sB = Nk; g.ldb = k;
+    g.C = w.Ysub; g.sC = Nk; g.ldc = k; g.skip = w.sub_done;
+    if ((rc = zgemm_f64(g, st))) return rc;
+    if ((rc = jacobi_svd(yd, st))) return rc;
+    g = gd(N, k, k, 2 * B);                     // V_f = V W
+    g.A = w.Vw; g.sA = Nk; g.lda = k; g.B = w.W; g.sB = kk; g.ldb = k; g.C = slot; g.sC = Nk;
+    g.ldc = k; g.skip = w.sub_done;
+    if ((rc = zgemm_f64(g, st))) return rc;
+    g = gd(N, k, N, 2 * B);                     // Z = M^+ U_y
+    g.opA = OP_C; g.A = w.M; g.sA = N2; g.lda = N;
+    g.B = w.Uy; g.sB = Nk; g.ldb = k; g.C = w.Zsub; g.sC = Nk; g.ldc = k; g.skip = w.sub_done;
+    if ((rc = zgemm_f64(g, st))) return rc;
+    IPEPS_LAUNCH(K_PROJ_PREP, 0, st,
+                 sub_residual_kernel<<<2 * B, 256, 0, st>>>(w.Zsub, slot, w.Sy, N, k, ncheck, 1e-12,
+                                                            w.sub_done, w.sub_rounds));
+    if (it + 1 == rounds) break;
+    IPEPS_LAUNCH(K_PROJ_PREP, 0, st,
+                 sub_refill_kernel<<<2 * B, 256, 0, st>>>(w.Zsub, N, k, c.seed, stream_id * 1000 + it,
+                                                          w.sub_done));
+    if ((rc = jacobi_svd(zd, st))) return rc;
+    IPEPS_LAUNCH(K_PROJ_PREP, 0, st,
+                 sub_fill_kernel<<<2 * B, 256, 0, st>>>(w.Vz, nullptr, N, k, 0, c.seed, 0, w.Vw,
+                                                        w.sub_done));
+  }
+  c.slot_warm[f][x] = true;
+  IPEPS_LAUNCH(K_PROJ_PREP, 0, st,
+               proj_prep_kernel<<<2 * B, 256, 0, st>>>(w.Sy, k, k, w.Uy, slot, N, chi, k, Nk, w.Us,
+                                                       w.Vs, w.kept, 1e-10, 1e-14, c.cut_rel));
+  return 0;
 }
 
 static int left_move(Ctx& c, int f, int x) {
@@ -408,15 +602,19 @@ static int left_move(Ctx& c, int f, int x) {
   g = gd(N, N, N, 2 * B);
   g.A = R; g.sA = N2; g.lda = N; g.B = Rt; g.sB = N2; g.ldb = N; g.C = w.M; g.sC = N2; g.ldc = N;
   if ((rc = zgemm_f64(g, st))) return rc;
-  // projector SVD (full one-sided Jacobi of M)
-  SvdDesc sd;
-  sd.m = N; sd.n = N; sd.batch = 2 * B;
-  sd.A = w.pA; sd.lda = N; sd.U = w.pU; sd.ldu = N; sd.S = w.pS; sd.V = w.pV; sd.ldv = N;
-  sd.tol = 4e-16 * N; sd.max_sweeps = 80; sd.err = c.derr; sd.sweeps_out = nullptr;
-  if ((rc = jacobi_svd(sd, st))) return rc;
-  proj_prep_kernel<<<2 * B, 256, 0, st>>>(w.S, w.U, w.V, N, chi, N, N2, w.Us, w.Vs, w.kept, 1e-10,
-                                          1e-14, c.cut_rel);
-  IPEPS_CUDA_TRY(cudaGetLastError());
+  if (!c.subspace) {
+    // projector SVD: full one-sided Jacobi of M
+    SvdDesc sd;
+    sd.m = N; sd.n = N; sd.batch = 2 * B;
+    sd.A = w.pA; sd.lda = N; sd.U = w.pU; sd.ldu = N; sd.S = w.pS; sd.V = w.pV; sd.ldv = N;
+    sd.tol = 4e-16 * N; sd.max_sweeps = 80; sd.err = c.derr; sd.sweeps_out = nullptr; sd.skip = nullptr;
+    if ((rc = jacobi_svd(sd, st))) return rc;
+    IPEPS_LAUNCH(K_PROJ_PREP, 0, st,
+                 proj_prep_kernel<<<2 * B, 256, 0, st>>>(w.S, N, N, w.U, w.V, N, chi, N, N2, w.Us,
+                                                         w.Vs, w.kept, 1e-10, 1e-14, c.cut_rel));
+  } else {
+    if ((rc = subspace_svd(c, f, x, R, Rt))) return rc;
+  }
   g = gd(N, chi, N, 2 * B);     // P = R~ Vs
   g.A = Rt; g.sA = N2; g.lda = N; g.B = w.Vs; g.sB = Nc; g.ldb = chi; g.C = w.P; g.sC = Nc; g.ldc = chi;
   if ((rc = zgemm_f64(g, st))) return rc;
@@ -459,8 +657,9 @@ static int left_move(Ctx& c, int f, int x) {
   g = gd(chi, chi, N, 2 * B);
   g.A = w.W1p; g.sA = T; g.lda = N; g.Bptr = m.c4B; g.ldb = chi; g.C = w.C4n; g.sC = chi2; g.ldc = chi;
   if ((rc = zgemm_f64(g, st))) return rc;
-  normalize_store_kernel<<<3 * 2 * B, 256, 0, st>>>(w.C1n, w.T4n, w.C4n, B, chi2, T, m.sC1, m.sT4,
-                                                   m.sC4, w.frozen, c.derr);
+  IPEPS_LAUNCH(K_NORM_STORE, 0, st,
+               normalize_store_kernel<<<3 * 2 * B, 256, 0, st>>>(w.C1n, w.T4n, w.C4n, B, chi2, T, m.sC1, m.sT4,
+                                                                m.sC4, w.frozen, c.derr));
   IPEPS_CUDA_TRY(cudaGetLastError());
   return 0;
 }
@@ -476,10 +675,11 @@ int ctm_spectra(Ctx& c, double tol, int first) {
   SvdDesc sd;
   sd.m = c.chi; sd.n = c.chi; sd.batch = 16 * c.B;
   sd.A = c.w.csA; sd.lda = c.chi; sd.U = nullptr; sd.ldu = 0; sd.S = c.w.csS; sd.V = nullptr; sd.ldv = 0;
-  sd.tol = 4e-16 * c.chi; sd.max_sweeps = 80; sd.err = c.derr; sd.sweeps_out = nullptr;
+  sd.tol = 4e-16 * c.chi; sd.max_sweeps = 80; sd.err = c.derr; sd.sweeps_out = nullptr; sd.skip = nullptr;
   if (int rc = jacobi_svd(sd, c.st)) return rc;
-  spectra_delta_kernel<<<c.B, 32, 0, c.st>>>(c.w.cs, c.w.prev, c.B, c.chi, first, tol, c.w.delta,
-                                             c.w.frozen, c.w.sweeps);
+  IPEPS_LAUNCH(K_SPECTRA, 0, c.st,
+               spectra_delta_kernel<<<c.B, 32, 0, c.st>>>(c.w.cs, c.w.prev, c.B, c.chi, first, tol, c.w.delta,
+                                                          c.w.frozen, c.w.sweeps));
   IPEPS_CUDA_TRY(cudaGetLastError());
   return 0;
 }

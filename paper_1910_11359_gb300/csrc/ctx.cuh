@@ -34,7 +34,7 @@ struct MoveOff {
 };
 struct CtmOff {
   MoveOff mv[4][2];
-  size_t csA, csS, pA, pU, pS, pV, envC, envT;
+  size_t csA, csS, pA, pU, pS, pV, envC, envT, yA, yU, yS, yV, zA, zU, zS;
 };
 
 struct CtmWork {
@@ -57,11 +57,23 @@ struct CtmWork {
   const cplx* const* pA; cplx* const* pU; double* const* pS; cplx* const* pV;
   // environment slots in (kind, pos, b) order for the initial environment [4 NPOS B]
   cplx* const* envC; cplx* const* envT;
+  // top-k projector SVD by subspace iteration (used when N > 2k): per (frame, column) slot the
+  // converged right vectors are kept as the next call's starting block
+  cplx* Vfin;                        // [4][2][2B][N k] right vectors per slot
+  cplx *Vw, *Ysub, *Uy, *W, *Zsub, *Vz;   // [2B][N k] / [2B][k k]
+  double *Sy, *Sz;                   // [2B][k]
+  int* sub_done;                     // [2B] converged flags of the subspace iteration
+  int* sub_rounds;                   // [2B] rounds used (diagnostics)
+  const cplx* const* yA; cplx* const* yU; double* const* yS; cplx* const* yV;   // Jacobi of Y
+  const cplx* const* zA; cplx* const* zU; double* const* zS;                    // Jacobi of Z
 };
 
 struct Ctx {
   // parameters
   int B = 1, dA = 2, d = 4, D = 2, D2 = 4, chi = 8, N = 32, order = 1, precision = 0;
+  int k = 32;              // projector subspace size (min(N, chi + 8))
+  bool subspace = false;   // top-k subspace iteration instead of the full Jacobi SVD of M
+  bool slot_warm[4][2] = {{false, false}, {false, false}, {false, false}, {false, false}};
   double dt = 0.02;
   double cut_rel = 1e-10;  // CTMRG projector truncation (relative)
   unsigned long long seed = 0;

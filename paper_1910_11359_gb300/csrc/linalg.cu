@@ -4,6 +4,7 @@
 #include <algorithm>
 
 #include "linalg.cuh"
+#include "prof.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -24,6 +25,7 @@ __device__ __forceinline__ cplx load_op(const cplx* P, long long ld, int op, int
 
 __global__ void __launch_bounds__(GT * GT) zgemm_kernel(GemmDesc g) {
   const int b = blockIdx.z;
+  if (g.skip && g.skip[b]) return;
   const cplx* A = g.Aptr ? g.Aptr[b] : g.A + (long long)b * g.sA;
   const cplx* B = g.Bptr ? g.Bptr[b] : g.B + (long long)b * g.sB;
   cplx* C = g.Cptr ? g.Cptr[b] : g.C + (long long)b * g.sC;
@@ -63,7 +65,8 @@ int zgemm_f64(const GemmDesc& g, cudaStream_t st) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return 0;
   if (g.batch > 65535) return cuda_fail(cudaErrorInvalidValue, "zgemm batch", __FILE__, __LINE__);
   dim3 grid((g.N + GT - 1) / GT, (g.M + GT - 1) / GT, g.batch);
-  zgemm_kernel<<<grid, GT * GT, 0, st>>>(g);
+  IPEPS_LAUNCH(K_ZGEMM, 8.0 * g.M * g.N * (double)g.K * g.batch, st,
+               zgemm_kernel<<<grid, GT * GT, 0, st>>>(g));
   IPEPS_CUDA_TRY(cudaGetLastError());
   return 0;
 }
@@ -108,7 +111,8 @@ int permute_c128(const cplx* in, cplx* out, int rank, const int* dims, const int
   if (n == 0) return 0;
   int threads = 256;
   long long blocks = std::min<long long>((n + threads - 1) / threads, 152LL * 16);
-  permute_kernel<<<(unsigned)blocks, threads, 0, st>>>(in, out, a, total, batch, s_in, s_out);
+  IPEPS_LAUNCH(K_PERMUTE, 0, st,
+               permute_kernel<<<(unsigned)blocks, threads, 0, st>>>(in, out, a, total, batch, s_in, s_out));
   IPEPS_CUDA_TRY(cudaGetLastError());
   return 0;
 }
@@ -123,6 +127,7 @@ constexpr int JTHREADS = 256;
 struct JacobiArgs {
   SvdDesc d;
   int np, ra, rw;
+  unsigned long long* flops;   // algorithmic flop counter (dot products + applied rotations)
 };
 
 // Round-robin ("circle") tournament: position 0 fixed, the rest rotate by one each round, so every
@@ -141,6 +146,8 @@ jacobi_kernel(JacobiArgs args) {
   const int npairs = np / 2;
   const int m = d.m, n = d.n;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = JTHREADS / 32;
+  // skipped problems: every CTA of the cluster reads the same flag and leaves before any barrier
+  if (d.skip && d.skip[prob]) return;
 
   extern __shared__ __align__(16) unsigned char jsm_raw[];
   cplx* colA = reinterpret_cast<cplx*>(jsm_raw);           // colA[j * ra + i]
@@ -164,6 +171,8 @@ jacobi_kernel(JacobiArgs args) {
 
   const int nrounds = np - 1;
   long long gcount = 0;
+  __shared__ int nrot_round;
+  double work = 0.0;   // flops of this problem, tallied by rank 0 / thread 0
   int sweep = 0;
   bool converged = false;
   for (sweep = 0; sweep < d.max_sweeps; ++sweep) {
@@ -192,6 +201,7 @@ jacobi_kernel(JacobiArgs args) {
           mypart[p * 4 + 2] = gr; mypart[p * 4 + 3] = gi;
         }
       }
+      if (tid == 0) nrot_round = 0;
       cluster.sync();
       // every CTA sums the partials in rank order, so all CTAs reach bit-identical decisions
       for (int p = tid; p < npairs; p += JTHREADS) {
@@ -219,10 +229,12 @@ jacobi_kernel(JacobiArgs args) {
           rot[p * 4 + 3] = -gis / gn;
           doit = 1;
           flags[npairs] = 1;
+          atomicAdd(&nrot_round, 1);
         }
         flags[p] = doit;
       }
       __syncthreads();
+      if (tid == 0) work += 16.0 * m * npairs + 14.0 * (m + n) * nrot_round;
       if (flags[npairs + 1]) break;
       const int rows = ra + rw;
       for (int idx = tid; idx < npairs * rows; idx += JTHREADS) {
@@ -299,6 +311,7 @@ jacobi_kernel(JacobiArgs args) {
     }
   }
   if (tid == 0 && rank == 0) {
+    if (args.flops) atomicAdd(args.flops, (unsigned long long)work);
     if (d.sweeps_out) d.sweeps_out[prob] = sweep + 1;
     if (d.err) {
       if (nonfinite_any) atomicOr(d.err, (unsigned)DEV_NONFINITE);
@@ -340,7 +353,8 @@ int jacobi_svd(const SvdDesc& d, cudaStream_t st) {
                                         200 * 1024 + 1024));
     attr_set = true;
   }
-  jacobi_kernel<<<d.batch * JCS, JTHREADS, smem, st>>>(a);
+  a.flops = prof_device_flops();
+  IPEPS_LAUNCH(K_JACOBI, 0, st, jacobi_kernel<<<d.batch * JCS, JTHREADS, smem, st>>>(a));
   IPEPS_CUDA_TRY(cudaGetLastError());
   return 0;
 }

@@ -19,6 +19,7 @@ struct GemmDesc {
   const cplx* A; const cplx* B; cplx* C;
   const cplx* const* Aptr; const cplx* const* Bptr; cplx* const* Cptr;
   cplx alpha, beta;
+  const int* skip;                // optional [batch]: problems with skip[b] != 0 are left untouched
 };
 
 int zgemm_f64(const GemmDesc& g, cudaStream_t st);
@@ -41,7 +42,8 @@ struct SvdDesc {
   double tol;          // rotate a pair when |a_p^+ a_q| > tol * ||a_p|| ||a_q||
   int max_sweeps;
   unsigned* err;       // device error word (DevErr bits)
-  int* sweeps_out;     // optional: sweeps used per problem
+  int* sweeps_out;     // optional: sweeps used per problem (1 = the input columns were orthogonal)
+  const int* skip;     // optional [batch]: problems with skip[b] != 0 are left untouched
 };
 
 int jacobi_svd(const SvdDesc& d, cudaStream_t st);

@@ -15,6 +15,7 @@
 
 #include "ctx.cuh"
 #include "measure.cuh"
+#include "prof.cuh"
 
 namespace ipeps {
 
@@ -233,8 +234,9 @@ int measure_run(Ctx& c, MeasureWork& w, const MeasurePlan& m, double* host_out) 
   for (int f = 0; f < 4; ++f)
     for (int l = 0; l < 2; ++l) {
       const cplx* A = l == 0 ? c.Aph : c.Bph;
-      open_layer_kernel<<<152 * 4, 256, 0, st>>>(A, d, c.D, B, 0, 0,
-                                                w.ao + (size_t)(f * 2 + l) * B * aoper, f);
+      IPEPS_LAUNCH(K_OPEN_LAYER, 0, st,
+                   open_layer_kernel<<<152 * 4, 256, 0, st>>>(A, d, c.D, B, 0, 0,
+                                                              w.ao + (size_t)(f * 2 + l) * B * aoper, f));
       IPEPS_CUDA_TRY(cudaGetLastError());
     }
   GemmDesc g = gdm(chi, D2 * chi, chi, 8 * B);         // tl = C1 T1
@@ -267,11 +269,13 @@ int measure_run(Ctx& c, MeasureWork& w, const MeasurePlan& m, double* host_out) 
   g = gdm(chi * D2, chi, chi, 2 * B);
   g.A = w.RCt; g.sA = T; g.lda = chi; g.Bptr = m.rcC; g.ldb = chi; g.C = w.RC; g.sC = T; g.ldc = chi;
   if ((rc = zgemm_f64(g, st))) return rc;
-  rho1_kernel<<<2 * B, 256, 0, st>>>(w.Lh, w.RC, chi, D2, d, w.rho1);
+  IPEPS_LAUNCH(K_RHO1, 8.0 * 2 * B * d * d * (double)chi * chi * D2, st,
+               rho1_kernel<<<2 * B, 256, 0, st>>>(w.Lh, w.RC, chi, D2, d, w.rho1));
   IPEPS_CUDA_TRY(cudaGetLastError());
-  rho2_kernel<<<4 * B * d * d * d * d, 256, 0, st>>>(m.r1, m.r2, chi, D2, d, w.rho2);
+  IPEPS_LAUNCH(K_RHO2, 8.0 * 4 * B * d * d * d * d * (double)chi * chi * D2, st,
+               rho2_kernel<<<4 * B * d * d * d * d, 256, 0, st>>>(m.r1, m.r2, chi, D2, d, w.rho2));
   IPEPS_CUDA_TRY(cudaGetLastError());
-  observables_kernel<<<B, 32, 0, st>>>(w.rho1, w.rho2, c.bondop, c.dh, B, d, c.dA, w.obs);
+  IPEPS_LAUNCH(K_OBS, 0, st, observables_kernel<<<B, 32, 0, st>>>(w.rho1, w.rho2, c.bondop, c.dh, B, d, c.dA, w.obs));
   IPEPS_CUDA_TRY(cudaGetLastError());
   IPEPS_CUDA_TRY(cudaMemcpyAsync(host_out, w.obs, sizeof(double) * 8 * B, cudaMemcpyDeviceToHost, st));
   IPEPS_CUDA_TRY(cudaStreamSynchronize(st));

@@ -2,6 +2,7 @@
 // double layers (paper Sec. "Set up for iPEPS": Eq. Hanc in hard-core boson form, Initialization,
 // Fig. 1).  Local basis s = n * d_A + a, d = 2 d_A; two-site index sA * d + sB.
 #include "model.cuh"
+#include "prof.cuh"
 
 namespace ipeps {
 
@@ -113,7 +114,7 @@ int build_gates(const double* J, const double* V, const double* h, const double*
   if (smem > 200 * 1024) return cuda_fail(cudaErrorInvalidValue, "gate size", __FILE__, __LINE__);
   IPEPS_CUDA_TRY(cudaFuncSetAttribute(gate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
-  gate_kernel<<<batch * ndelta, 256, smem, st>>>(J, V, h, deltas, ndelta, d, dA, out);
+  IPEPS_LAUNCH(K_GATE, 0, st, gate_kernel<<<batch * ndelta, 256, smem, st>>>(J, V, h, deltas, ndelta, d, dA, out));
   IPEPS_CUDA_TRY(cudaGetLastError());
   return 0;
 }
@@ -127,7 +128,7 @@ __global__ void bond_op_kernel(const double* J, const double* V, int d, int dA, 
 
 int build_bond_ops(const double* J, const double* V, int batch, int d, int dA, cplx* out,
                    cudaStream_t st) {
-  bond_op_kernel<<<batch, 256, 0, st>>>(J, V, d, dA, out);
+  IPEPS_LAUNCH(K_BONDOP, 0, st, bond_op_kernel<<<batch, 256, 0, st>>>(J, V, d, dA, out));
   IPEPS_CUDA_TRY(cudaGetLastError());
   return 0;
 }
@@ -151,7 +152,7 @@ __global__ void init_state_kernel(cplx* GA, cplx* GB, double* lam, int d, int dA
 }
 
 int init_state(cplx* GA, cplx* GB, double* lam, int d, int dA, int D, int batch, cudaStream_t st) {
-  init_state_kernel<<<64, 256, 0, st>>>(GA, GB, lam, d, dA, D, batch);
+  IPEPS_LAUNCH(K_INIT_STATE, 0, st, init_state_kernel<<<64, 256, 0, st>>>(GA, GB, lam, d, dA, D, batch));
   IPEPS_CUDA_TRY(cudaGetLastError());
   return 0;
 }
@@ -177,7 +178,7 @@ __global__ void phys_kernel(const cplx* GA, const cplx* GB, const double* lam, c
 
 int physical_tensors(const cplx* GA, const cplx* GB, const double* lam, cplx* A, cplx* B, int d, int D,
                      int batch, cudaStream_t st) {
-  phys_kernel<<<152 * 4, 256, 0, st>>>(GA, GB, lam, A, B, d, D, batch);
+  IPEPS_LAUNCH(K_PHYS, 0, st, phys_kernel<<<152 * 4, 256, 0, st>>>(GA, GB, lam, A, B, d, D, batch));
   IPEPS_CUDA_TRY(cudaGetLastError());
   return 0;
 }
@@ -217,7 +218,9 @@ __global__ void double_layer_kernel(const cplx* A, cplx* out, int d, int D, int 
 }
 
 int double_layers(const cplx* A, cplx* out, int d, int D, int batch, int nrot, cudaStream_t st) {
-  double_layer_kernel<<<152 * 8, 256, 0, st>>>(A, out, d, D, batch, nrot);
+  const double D8 = (double)D * D * D * D * D * D * D * D;
+  IPEPS_LAUNCH(K_DLAYER, 8.0 * d * D8 * batch, st,
+               double_layer_kernel<<<152 * 8, 256, 0, st>>>(A, out, d, D, batch, nrot));
   IPEPS_CUDA_TRY(cudaGetLastError());
   return 0;
 }

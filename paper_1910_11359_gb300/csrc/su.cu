@@ -5,6 +5,7 @@
 // SVD truncates theta back to D, and U_A / U_B map the kept vectors back to full site tensors.  The
 // nonzero singular values equal those of the unreduced two-site tensor.
 #include "su.cuh"
+#include "prof.cuh"
 
 namespace ipeps {
 
@@ -159,25 +160,29 @@ int su_bond_update(SuWork& w, cplx* GA, cplx* GB, double* lam, double* eps, cons
   const int D3 = D * D * D, n = d * D, nt = n * d;
   if (D3 < n) return cuda_fail(cudaErrorInvalidValue, "simple update needs D^3 >= d D", __FILE__, __LINE__);
   const int blocks = 152 * 4, threads = 256;
-  su_absorb_kernel<<<blocks, threads, 0, st>>>(GA, GB, lam, legA, d, D, batch, w.Amat, w.Bmat);
+  IPEPS_LAUNCH(K_SU_ABSORB, 0, st,
+               su_absorb_kernel<<<blocks, threads, 0, st>>>(GA, GB, lam, legA, d, D, batch, w.Amat, w.Bmat));
   IPEPS_CUDA_TRY(cudaGetLastError());
   // factorise both absorbed tensors in one batch of 2B problems
   SvdDesc q;
   q.m = D3; q.n = n; q.batch = 2 * batch;
   q.A = w.qA; q.lda = n; q.U = w.qU; q.ldu = n; q.S = w.qS; q.V = w.qV; q.ldv = n;
-  q.tol = 4e-16 * D3; q.max_sweeps = 60; q.err = err; q.sweeps_out = nullptr;
+  q.tol = 4e-16 * D3; q.max_sweeps = 60; q.err = err; q.sweeps_out = nullptr; q.skip = nullptr;
   if (int rc = jacobi_svd(q, st)) return rc;
-  su_theta_kernel<<<blocks, threads, 0, st>>>(w.SA, w.VA, w.SB, w.VB, lam, gate, legA, d, D, batch, w.theta);
+  IPEPS_LAUNCH(K_SU_THETA, 8.0 * batch * (double)nt * nt * d * d * (D + 1), st,
+               su_theta_kernel<<<blocks, threads, 0, st>>>(w.SA, w.VA, w.SB, w.VB, lam, gate, legA, d, D, batch, w.theta));
   IPEPS_CUDA_TRY(cudaGetLastError());
   SvdDesc t;
   t.m = nt; t.n = nt; t.batch = batch;
   t.A = w.tA; t.lda = nt; t.U = w.tU; t.ldu = nt; t.S = w.tS; t.V = w.tV; t.ldv = nt;
-  t.tol = 4e-16 * nt; t.max_sweeps = 60; t.err = err; t.sweeps_out = nullptr;
+  t.tol = 4e-16 * nt; t.max_sweeps = 60; t.err = err; t.sweeps_out = nullptr; t.skip = nullptr;
   if (int rc = jacobi_svd(t, st)) return rc;
-  su_truncate_kernel<<<batch, 32, 0, st>>>(w.Stheta, nt, D, legA, lam, eps, w.kept, 1e-10, 1e-14);
+  IPEPS_LAUNCH(K_SU_TRUNCATE, 0, st,
+               su_truncate_kernel<<<batch, 32, 0, st>>>(w.Stheta, nt, D, legA, lam, eps, w.kept, 1e-10, 1e-14));
   IPEPS_CUDA_TRY(cudaGetLastError());
-  su_rebuild_kernel<<<blocks, threads, 0, st>>>(w.UA, w.UB, w.X, w.Y, lam, w.kept, legA, d, D, batch,
-                                               GA, GB, 1e-14);
+  IPEPS_LAUNCH(K_SU_REBUILD, 16.0 * batch * d * (double)D3 * D * n, st,
+               su_rebuild_kernel<<<blocks, threads, 0, st>>>(w.UA, w.UB, w.X, w.Y, lam, w.kept, legA, d, D, batch,
+                                                            GA, GB, 1e-14));
   IPEPS_CUDA_TRY(cudaGetLastError());
   return 0;
 }
