@@ -21,6 +21,20 @@ int ipeps_kernel_zgemm(int M, int N, int K, int batch, int opA, int opB,
                        const double* B, long long ldb, long long sB,
                        double* C, long long ldc, long long sC, void* stream);
 
+/* Allocation-free variant of ipeps_kernel_svd, same arguments and results.  The paper has no
+ * counterpart: this exists for callers that cannot call cudaMalloc (an application allocator owns the
+ * device memory, a plug-in only receives pre-allocated buffers, or device allocation is forbidden
+ * after start-up).  Instead of allocating its operand pointer tables and error word per call, it
+ * uses a fixed array in device global memory (about 33 KB per GPU that loads the library, kept
+ * until the process exits), so batch is limited to 1024 problems; larger batches are rejected with
+ * IPEPS_EINVAL.  A, U, S, V (and sweeps_out) are still caller-provided device buffers.  The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  All calls share the array and the last
+ * call's contents stay in it (the error word is cleared at the start of every call); calls whose
+ * GPU work overlaps race on it and must be serialised by the caller.  Synchronises `stream`. */
+int ipeps_kernel_svd_noalloc(int m, int n, int batch, const double* A, double* U, double* S,
+                             double* V, double tol, int max_sweeps, int* sweeps_out, void* stream);
+
 /* Trotter gate exp(-i h_b delta) of the d = 4 dilated model (J, V, h as in ipeps_params),
  * computed on the device and copied to the HOST buffer out (16 x 16 complex, row index sA*4+sB).
  * Allocates and frees a small device buffer; synchronising. */
