@@ -54,6 +54,11 @@ from .su import truncation_rank
 ein = functools.partial(np.einsum, optimize=True)
 
 PROJ_CUT_REL = 1e-10
+# Multiplets at the chi cut (C8 reading): a computed singular value of M is accurate to about
+# eps * s_1 in absolute terms, so for values below ~1e-5 s_1 a relative gap of 1e-10 lies inside the
+# rounding noise; two values whose absolute gap is below PROJ_DEGEN_ABS * s_1 also count as one
+# multiplet, so that the decision does not depend on rounding.
+PROJ_DEGEN_ABS = 1e-11
 
 
 # ----------------------------------------------------------------------------- double layer
@@ -196,7 +201,7 @@ def projectors(R, Rt, chi, cut_rel=PROJ_CUT_REL):
     s is the full singular spectrum of M = R R~ (for diagnostics)."""
     M = R @ Rt
     U, s, Vh = np.linalg.svd(M)
-    K = truncation_rank(s, chi)
+    K = truncation_rank(s, chi, degen_abs=PROJ_DEGEN_ABS)
     K = min(K, int(np.sum(s > cut_rel * s[0]))) if s[0] > 0 else 0
     K = max(K, 1) if s[0] > 0 else 0
     N = R.shape[1]
@@ -272,10 +277,21 @@ def spectra_delta(s_new, s_old):
     return max(np.linalg.norm(s_new[k] - s_old[k]) for k in s_new)
 
 
-def ctmrg(a, env, chi, tol=1e-10, max_sweeps=200, min_sweeps=1, cut_rel=PROJ_CUT_REL):
-    """Sweep until the corner spectra change by less than ``tol``; returns (env, sweeps, delta)."""
+STALL_WINDOW = 10      # sweeps without a factor-2 improvement of the best delta
+STALL_MAX = 1e-7       # ... counted as a stall only once the best delta is below this
+
+
+def ctmrg(a, env, chi, tol=1e-10, max_sweeps=200, min_sweeps=1, cut_rel=PROJ_CUT_REL,
+          stall_window=STALL_WINDOW, stall_max=STALL_MAX):
+    """Sweep until the corner spectra change by less than ``tol``; returns (env, sweeps, delta).
+
+    The paper asks for a "sufficiently well-converged" environment (Appendix).  Reading: stop at
+    delta < tol, or when delta has stalled at its rounding floor -- no factor-2 improvement of the
+    best delta for ``stall_window`` sweeps while that best is already below ``stall_max``.  With
+    tol <= 0 exactly max_sweeps sweeps run (no stall test)."""
     prev = corner_spectra(env, chi)
     delta = np.inf
+    best, since = np.inf, 0
     n = 0
     for n in range(1, max_sweeps + 1):
         env = sweep(a, env, chi, cut_rel)
@@ -283,6 +299,12 @@ def ctmrg(a, env, chi, tol=1e-10, max_sweeps=200, min_sweeps=1, cut_rel=PROJ_CUT
         delta = spectra_delta(cur, prev)
         prev = cur
         if n >= min_sweeps and delta < tol:
+            break
+        if delta < 0.5 * best:
+            best, since = delta, 0
+        else:
+            since += 1
+        if tol > 0 and since >= stall_window and best < stall_max:
             break
     return env, n, delta
 

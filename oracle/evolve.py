@@ -32,10 +32,15 @@ def converge_and_measure(GA, GB, lam, env, p, tol, max_sweeps):
     return env, obs
 
 
-def run(p, tol=1e-10, max_sweeps=500, callback=None):
+def run(p, tol=1e-10, max_sweeps=500, callback=None, cold=False):
     """Evolve with parameters p (J, V, h, D, chi, order, dt, t_max, meas_every[, d_A, cut_rel]).
 
-    Returns a list of observation dicts at t = 0, meas_every, 2 meas_every, ... t_max.
+    Returns a list of observation dicts at t = 0, meas_every, 2 meas_every, ... t_max.  With
+    ``cold`` each dict also holds, under 'cold', the readout converged from the traced start of
+    that time's tensors instead of the previous environment.  The cold readout depends only on the
+    state; the warm one can also depend on the simple update's gauge (the phases of its singular
+    vectors), because at some times the truncated CTMRG has several fixed points and the previous
+    environment selects one of them.
     """
     d_A = p.get('d_A', 2)
     GA, GB, lam = model.initial_tensors(p['D'], d_A)
@@ -50,6 +55,8 @@ def run(p, tol=1e-10, max_sweeps=500, callback=None):
         if step % stride == 0:
             env, obs = converge_and_measure(GA, GB, lam, env, p, tol, max_sweeps)
             obs.update(t=step * p['dt'], trunc_err_acc=eps_acc, lam=lam.copy())
+            if cold:
+                obs['cold'] = converge_and_measure(GA, GB, lam, None, p, tol, max_sweeps)[1]
             out.append(obs)
             if callback is not None:
                 callback(obs)

@@ -44,15 +44,17 @@ def trotter_sequence(order, dt):
     raise ValueError("trotter order must be 1 or 2")
 
 
-def truncation_rank(s, keep, degen_rtol=DEGEN_RTOL, tiny_rel=TINY_REL):
+def truncation_rank(s, keep, degen_rtol=DEGEN_RTOL, tiny_rel=TINY_REL, degen_abs=0.0):
     """Number of singular values kept at a cut of nominal size ``keep``.
 
     If the last kept and first dropped values form one multiplet (relative gap below
-    ``degen_rtol``) and the dropped one is not numerically zero, the cut moves down to the
-    multiplet's upper edge, so that a multiplet is never split.
+    ``degen_rtol``, or absolute gap below ``degen_abs`` times the largest value) and the dropped
+    one is not numerically zero, the cut moves down to the multiplet's upper edge, so that a
+    multiplet is never split.
     """
     K = min(keep, len(s))
-    while 1 < K < len(s) and s[K] > tiny_rel * s[0] and s[K - 1] / s[K] - 1.0 < degen_rtol:
+    while 1 < K < len(s) and s[K] > tiny_rel * s[0] and (
+            s[K - 1] / s[K] - 1.0 < degen_rtol or s[K - 1] - s[K] < degen_abs * s[0]):
         K -= 1
     return K
 

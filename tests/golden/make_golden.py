@@ -3,6 +3,7 @@
     python tests/golden/make_golden.py config1      -> tests/golden/config1_oracle.json
     python tests/golden/make_golden.py config1cut   -> tests/golden/config1_cut1e-6_oracle.json
     python tests/golden/make_golden.py config2      -> tests/golden/config2_h{1,5,10}_oracle.json
+    python tests/golden/make_golden.py config2@5    -> tests/golden/config2_h5_oracle.json only
 
 Workloads: inputs.CONFIG1 (D=2, chi=8, first order dt=0.02 to t=1, measured every 0.1) and
 inputs.CONFIG2 (D=3, chi=18, second order dt=0.05 to t=5, measured every 0.25, h in {1,5,10}).
@@ -28,6 +29,8 @@ def _dump(path, params, out, seconds):
     for o in out:
         r = {k: float(o[k]) for k in KEYS}
         r["lam"] = [[float(x) for x in row] for row in o["lam"]]
+        # the same readout converged from the traced start (gauge independent, see evolve.run)
+        r["cold"] = {k: float(o["cold"][k]) for k in KEYS if k in o["cold"]}
         rows.append(r)
     with open(path, "w") as f:
         json.dump(dict(params=params, oracle_seconds=seconds, rows=rows), f, indent=1)
@@ -37,23 +40,26 @@ def run(name):
     if name == "config1":
         p = dict(CONFIG1)
         t0 = time.time()
-        out = evolve.run(p, tol=p["tol"])
+        out = evolve.run(p, tol=p["tol"], cold=True)
         _dump(os.path.join(HERE, "config1_oracle.json"), p, out, time.time() - t0)
     elif name == "config1cut":
         p = dict(CONFIG1, cut_rel=1e-6)
         t0 = time.time()
-        out = evolve.run(p, tol=p["tol"])
+        out = evolve.run(p, tol=p["tol"], cold=True)
         _dump(os.path.join(HERE, "config1_cut1e-6_oracle.json"), p, out, time.time() - t0)
     elif name.startswith("config2"):
-        # "config2" = the full workload; "config2:T" stops at t = T (same trajectory, fewer points)
+        # "config2" = the full workload; "config2:T" stops at t = T (same trajectory, fewer points);
+        # "config2@H" writes only the instance with h = H (the instances are independent)
         t_max = float(name.split(":")[1]) if ":" in name else CONFIG2["t_max"]
-        for h in CONFIG2["hs"]:
+        hs = [float(name.split("@")[1])] if "@" in name else CONFIG2["hs"]
+        for h in hs:
             p = {k: v for k, v in CONFIG2.items() if k != "hs"}
             p["h"] = h
             p["t_max"] = t_max
             t0 = time.time()
-            out = evolve.run(p, tol=p["tol"], callback=lambda o: print(name, h, o["t"],
-                                                                      o["imbalance"], flush=True))
+            out = evolve.run(p, tol=p["tol"], cold=True,
+                             callback=lambda o: print(name, h, o["t"], o["imbalance"],
+                                                      o["cold"]["imbalance"], flush=True))
             _dump(os.path.join(HERE, "config2_h%d_oracle.json" % int(h)), p, out, time.time() - t0)
     else:
         raise SystemExit("unknown workload " + name)
