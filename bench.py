@@ -49,6 +49,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("native", "reference"), default="native")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--workload", choices=("quench", "ctmrg"), default="quench",
+                    help="quench: the Trotter+CTMRG readout workload (default); ctmrg: the standalone "
+                         "CTMRG contraction benchmark on random tensors")
+    ap.add_argument("--D", type=int, default=4, help="ctmrg workload: bond dimension (chi = 2 D^2)")
+    ap.add_argument("--precision", choices=("fp64", "split"), default="fp64")
     return ap.parse_args()
 
 
@@ -284,10 +289,99 @@ def native_main(args):
     return 0
 
 
+def contraction_flops_per_sweep(D, chi):
+    """Algorithmic real flops of one sweep's contractions (16 projector computations, explicit
+    double layer; SVDs excluded): per projector 4 enlarged corners (C T: chi^2 D2 chi, T X1:
+    chi D2 chi D2 chi, X2 a: chi^2 D2^4), 3 N^3 products, the projector products (2 N^2 chi) and the
+    absorption (C1: chi N chi; T4: chi D2 chi chi + chi^2 D2^4 + chi N D2 chi; C4: chi D2 chi chi +
+    chi N chi) -- counted for the two cuts a move computes, complex multiply-add = 8 flops."""
+    D2 = D * D
+    N = chi * D2
+    corner = chi * chi * D2 * chi + chi * D2 * chi * D2 * chi + chi * chi * D2 ** 4
+    per_cut = 4 * corner + 3 * N ** 3 + 2 * N * N * chi
+    absorb = chi * N * chi + (chi * D2 * chi * chi + chi * chi * D2 ** 4 + chi * N * D2 * chi) \
+        + (chi * D2 * chi * chi + chi * N * chi)
+    return 8.0 * 8 * 2 * (per_cut + absorb)          # 8 moves x 2 cuts
+
+
+def ctmrg_main(args):
+    """Standalone CTMRG contraction benchmark: random (4, D, D, D, D) tensors, chi = 2 D^2, 20 sweeps
+    per step from the traced start."""
+    import torch
+    import paper_1910_11359_gb300 as pkg
+    from inputs import config3_tensors
+
+    D = args.D
+    chi = 2 * D * D
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    stream = torch.cuda.Stream()
+    prec = pkg.SPLIT_BF16X3 if args.precision == "split" else pkg.FP64
+    A, B = config3_tensors(D)
+    sim = pkg.IPEPS([1.0], [1.0], [5.0], D=D, chi=chi, order=2, dt=0.05, precision=prec,
+                    stream=stream.cuda_stream)
+    sim.set_tensors(A[None], B[None], None)
+    sweeps = 20
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            sim.ctmrg_reset()
+            sim.ctmrg_converge(tol=0.0, max_sweeps=sweeps)
+        torch.cuda.synchronize()
+        pkg.profile_enable(True)
+        launches0 = pkg.launch_count()
+        total = 0.0
+        for _ in range(args.steps):
+            sim.ctmrg_reset()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sim.ctmrg_converge(tol=0.0, max_sweeps=sweeps)
+            e1.record(stream)
+            e1.synchronize()
+            total += e0.elapsed_time(e1)
+        prof = pkg.profile_read()
+        pkg.profile_enable(False)
+        launches = pkg.launch_count() - launches0
+        obs = sim.measure()[0]
+    sim.close()
+    flops = contraction_flops_per_sweep(D, chi) * sweeps * args.steps
+    dom = max(prof.items(), key=lambda kv: kv[1][0])
+    name, (ms, fl, n) = dom
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    bf16_peak = peaks.get("bf16_tflops", 1900.0)
+    if name == "tc_gemm_bf16":
+        peak, bound, unit = bf16_peak, "tensor", "TFLOP/s"
+    else:
+        peak, bound, unit = pkg.fp64_peak_tflops(), "alu", "TFLOP/s"
+    tc_ms, tc_fl, tc_n = prof.get("tc_gemm_bf16", (0.0, 0.0, 0))
+    line = {"metric": "CTMRG sweeps/s", "value": sweeps * args.steps / (total * 1e-3),
+            "unit": "sweeps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16x3" if prec else "f64", "data": "synthetic",
+            "config": {"workload": "CTMRG contraction, random (4,D,D,D,D), D=%d chi=%d, 20 sweeps" % (D, chi),
+                       "precision": args.precision},
+            "contraction_tflops": flops / (total * 1e-3) / 1e12,
+            "roofline": {"bound": bound, "kernel": name, "achieved": fl / (ms * 1e-3) / 1e12 if ms else 0,
+                         "peak": peak, "unit": unit, "frac": (fl / (ms * 1e-3) / 1e12) / peak if ms else 0,
+                         "launches": n, "avg_launch_us": 1e3 * ms / max(n, 1)},
+            "tensor_core_gemm": None if not tc_n else {
+                "kernel": "tc_gemm_bf16", "launches": tc_n, "avg_launch_us": 1e3 * tc_ms / tc_n,
+                "executed_tflops": tc_fl / (tc_ms * 1e-3) / 1e12, "peak": bf16_peak,
+                "frac": tc_fl / (tc_ms * 1e-3) / 1e12 / bf16_peak,
+                "peak_source": "MEASURED_PEAKS.json bf16 burst" if peaks else "fallback"},
+            "kernel_time_share": {k: round(v[0] / total, 4) for k, v in
+                                  sorted(prof.items(), key=lambda kv: -kv[1][0]) if v[0] > 0},
+            "gpu_launches": int(launches), "imbalance_after": obs["imbalance"]}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_main(args)
+    if args.workload == "ctmrg":
+        return ctmrg_main(args)
     return native_main(args)
 
 

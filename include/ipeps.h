@@ -89,12 +89,14 @@ ipeps_status ipeps_set_tensors(ipeps_h h, const double* gamma_A, const double* g
 ipeps_status ipeps_trotter_step(ipeps_h h, int n_steps, double* trunc_err_out);
 
 /* CTMRG environment of the current tensors (Sec. "Set up for iPEPS", Readout; Appendix: chi >= D^2,
- * converged).  Directional moves with full 2x2-block projectors; sweeps until the normalised corner
- * spectra change by less than tol (per instance; converged instances stop updating), at most
- * max_sweeps.  tol <= 0 runs exactly max_sweeps sweeps.  The first call starts from the traced
+ * "sufficiently well converged").  Directional moves with full 2x2-block projectors; per instance,
+ * sweeps until the normalised corner spectra change by less than tol, or until that change has
+ * stalled at its rounding floor (no factor-2 improvement of its best value for 10 sweeps while the
+ * best is below 1e-7); converged instances stop updating; at most max_sweeps sweeps.  tol <= 0 runs
+ * exactly max_sweeps sweeps.  The first call starts from the traced
  * double layers, later calls from the previous environment.  sweeps_out: host int[batch] or NULL;
- * delta_out: host double[batch] or NULL.  Returns IPEPS_ENOCONV when an instance did not converge
- * (its environment is still usable). */
+ * delta_out: host double[batch] or NULL (last change).  Returns IPEPS_ENOCONV when an instance
+ * reached max_sweeps without converging (its environment is still usable). */
 ipeps_status ctmrg_converge(ipeps_h h, double tol, int max_sweeps, int* sweeps_out, double* delta_out);
 
 /* Discard the environment; the next ctmrg_converge starts from the traced double layers. */

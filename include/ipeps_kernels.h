@@ -40,6 +40,16 @@ int ipeps_kernel_svd_noalloc(int m, int n, int batch, const double* A, double* U
  * Allocates and frees a small device buffer; synchronising. */
 int ipeps_kernel_gate(double J, double V, double h, double delta, double* out);
 
+/* Same product as ipeps_kernel_zgemm on the tcgen05 tensor cores in split precision: the complex
+ * product is embedded as one real GEMM ([[Ar,-Ai],[Ai,Ar]] [Br;Bi]), every value is split into two
+ * BF16 terms hi + lo, the three leading products hi*hi + hi*lo + lo*hi are accumulated in FP32 in
+ * tensor memory.  Relative error ~1e-5 of the operand scale.  Allocates and frees its workspace;
+ * synchronising; IPEPS_ETIMEOUT if a bounded device-side wait ran out. */
+int ipeps_kernel_zgemm_split(int M, int N, int K, int batch, int opA, int opB,
+                             const double* A, long long lda, long long sA,
+                             const double* B, long long ldb, long long sB,
+                             double* C, long long ldc, long long sC, void* stream);
+
 /* out = in permuted: out axis j is in axis perm[j] (rank <= 8, dims[] of the input). */
 int ipeps_kernel_permute(const double* in, double* out, int rank, const int* dims,
                          const int* perm, int batch, long long s_in, long long s_out, void* stream);

@@ -46,7 +46,7 @@ EXPORTS = ["ipeps_init", "ipeps_set_tensors", "ipeps_trotter_step", "ctmrg_conve
            "ipeps_footprint_bytes", "ipeps_destroy", "ipeps_last_error", "ipeps_kernel_zgemm",
            "ipeps_kernel_permute", "ipeps_kernel_svd", "ipeps_kernel_gate", "ipeps_launch_count",
            "ipeps_profile_enable", "ipeps_profile_classes", "ipeps_profile_name", "ipeps_profile_read",
-           "ipeps_kernel_fp64_peak", "ipeps_kernel_svd_noalloc"]
+           "ipeps_kernel_fp64_peak", "ipeps_kernel_svd_noalloc", "ipeps_kernel_zgemm_split"]
 
 
 def lib():
@@ -86,6 +86,7 @@ def lib():
     L.ipeps_profile_read.argtypes = [dp, dp, P(ctypes.c_ulonglong)]
     L.ipeps_kernel_fp64_peak.argtypes = [dp]
     L.ipeps_kernel_svd_noalloc.argtypes = [i, i, i, vp, vp, vp, vp, d, i, vp, vp]
+    L.ipeps_kernel_zgemm_split.argtypes = [i, i, i, i, i, i, vp, ll, ll, vp, ll, ll, vp, ll, ll, vp]
     for name in EXPORTS:
         if name not in ("ipeps_last_error", "ipeps_launch_count", "ipeps_profile_name"):
             getattr(L, name).restype = ctypes.c_int

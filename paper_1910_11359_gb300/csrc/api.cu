@@ -9,6 +9,7 @@
 #include "ctx.cuh"
 #include "measure.cuh"
 #include "model.cuh"
+#include "tc_gemm.cuh"
 
 using namespace ipeps;
 
@@ -49,6 +50,7 @@ ipeps_status check_dev(ipeps_h h) {
     if (e & DEV_NONFINITE) return fail(h, IPEPS_ENAN, "non-finite value in a device kernel");
     if (e & DEV_JACOBI_CAP) return fail(h, IPEPS_ENOCONV, "Jacobi SVD hit its sweep limit");
     if (e & DEV_BAD_SIZE) return fail(h, IPEPS_EINVAL, "device kernel rejected a size");
+    if (e & DEV_TIMEOUT) return fail(h, IPEPS_ETIMEOUT, "a bounded device-side wait ran out");
   }
   return IPEPS_OK;
 }
@@ -61,7 +63,10 @@ ipeps_status validate(const ipeps_params* p, std::string* why) {
   if (p->chi < p->D * p->D) { *why = "chi must be >= D^2"; return IPEPS_EINVAL; }
   if (p->trotter_order != 1 && p->trotter_order != 2) { *why = "trotter_order must be 1 or 2"; return IPEPS_EINVAL; }
   if (!(p->dt > 0.0)) { *why = "dt must be > 0"; return IPEPS_EINVAL; }
-  if (p->precision != IPEPS_FP64) { *why = "this build implements precision = IPEPS_FP64 only"; return IPEPS_EUNSUPPORTED; }
+  if (p->precision != IPEPS_FP64 && p->precision != IPEPS_SPLIT_BF16X3) {
+    *why = "precision must be IPEPS_FP64 or IPEPS_SPLIT_BF16X3";
+    return IPEPS_EUNSUPPORTED;
+  }
   if (!p->J || !p->V || !p->h) { *why = "J, V, h arrays are required"; return IPEPS_EINVAL; }
   const int N = p->chi * p->D * p->D;
   const int k = p->chi + 8 < N ? p->chi + 8 : N;
@@ -318,6 +323,7 @@ ipeps_status ctmrg_converge(ipeps_h h, double tol, int max_sweeps, int* sweeps_o
   cudaMemcpyAsync(h->last_sweeps.data(), c.w.sweeps, sizeof(int) * B, cudaMemcpyDeviceToHost, c.st);
   cudaMemcpyAsync(h->last_delta.data(), c.w.delta, sizeof(double) * B, cudaMemcpyDeviceToHost, c.st);
   cudaMemcpyAsync(h->last_eps.data(), c.eps, sizeof(double) * B, cudaMemcpyDeviceToHost, c.st);
+  cudaMemcpyAsync(frozen.data(), c.w.frozen, sizeof(int) * B, cudaMemcpyDeviceToHost, c.st);
   ipeps_status st = check_dev(h);
   h->t_measured = c.t;
   if (st != IPEPS_OK && st != IPEPS_ENOCONV) return st;
@@ -325,7 +331,7 @@ ipeps_status ctmrg_converge(ipeps_h h, double tol, int max_sweeps, int* sweeps_o
   if (delta_out) memcpy(delta_out, h->last_delta.data(), sizeof(double) * B);
   if (tol > 0.0)
     for (int b = 0; b < B; ++b)
-      if (!(h->last_delta[b] < tol)) return fail(h, IPEPS_ENOCONV, "CTMRG did not reach tol");
+      if (!frozen[b]) return fail(h, IPEPS_ENOCONV, "CTMRG reached max_sweeps without converging");
   return st;
 }
 
@@ -420,6 +426,41 @@ int ipeps_kernel_gate(double J, double V, double h, double delta, double* out) {
     rc = cuda_fail(cudaGetLastError(), "gate copy", __FILE__, __LINE__);
   cudaFree(dbuf);
   return rc;
+}
+
+int ipeps_kernel_zgemm_split(int M, int N, int K, int batch, int opA, int opB, const double* A,
+                             long long lda, long long sA, const double* B, long long ldb, long long sB,
+                             double* C, long long ldc, long long sC, void* stream) {
+  GemmDesc g;
+  memset(&g, 0, sizeof(g));
+  g.M = M; g.N = N; g.K = K; g.batch = batch; g.opA = opA; g.opB = opB;
+  g.A = (const cplx*)A; g.lda = lda; g.sA = sA;
+  g.B = (const cplx*)B; g.ldb = ldb; g.sB = sB;
+  g.C = (cplx*)C; g.ldc = ldc; g.sC = sC;
+  g.alpha = cmk(1.0, 0.0); g.beta = cmk(0.0, 0.0);
+  const size_t bytes = tc::split_workspace_bytes(M, N, K, batch);
+  void* work = nullptr;
+  unsigned* derr = nullptr;
+  if (cudaMalloc(&work, bytes) != cudaSuccess || cudaMalloc(&derr, sizeof(unsigned)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(work);
+    set_thread_error("cudaMalloc failed");
+    return IPEPS_ENOMEM;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaMemsetAsync(derr, 0, sizeof(unsigned), st);
+  int rc = tc::zgemm_split_bf16(g, work, bytes, derr, st);
+  unsigned e = 0;
+  if (!rc) {
+    if (cudaMemcpyAsync(&e, derr, sizeof(unsigned), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      rc = cuda_fail(cudaGetLastError(), "split gemm sync", __FILE__, __LINE__);
+  }
+  cudaFree(work);
+  cudaFree(derr);
+  if (rc) return rc;
+  if (e & DEV_TIMEOUT) { set_thread_error("tensor-core GEMM wait timed out"); return IPEPS_ETIMEOUT; }
+  return 0;
 }
 
 int ipeps_kernel_permute(const double* in, double* out, int rank, const int* dims, const int* perm,

@@ -42,6 +42,7 @@ enum DevErr : unsigned {
   DEV_NONFINITE = 1u,
   DEV_JACOBI_CAP = 2u,
   DEV_BAD_SIZE = 4u,
+  DEV_TIMEOUT = 8u,
 };
 
 }  // namespace ipeps

@@ -28,6 +28,7 @@
 #include "ctx.cuh"
 #include "model.cuh"
 #include "prof.cuh"
+#include "tc_gemm.cuh"
 
 namespace ipeps {
 
@@ -79,6 +80,8 @@ void ctm_carve(Ctx& c) {
   w.frozen = a.take<int>(B);
   w.sweeps = a.take<int>(B);
   w.have_prev = a.take<int>(1);
+  w.best = a.take<double>(B);
+  w.since = a.take<int>(B);
   const long long Nk = (long long)c.N * c.k, kk = (long long)c.k * c.k;
   w.Vfin = a.take<cplx>((size_t)8 * 2 * B * Nk);
   w.Vw = a.take<cplx>((size_t)2 * B * Nk);
@@ -91,6 +94,23 @@ void ctm_carve(Ctx& c) {
   w.Sz = a.take<double>((size_t)2 * B * c.k);
   w.sub_done = a.take<int>((size_t)2 * B);
   w.sub_rounds = a.take<int>((size_t)2 * B);
+  w.sub_res = a.take<double>((size_t)2 * B);
+  if (c.precision == 1) {
+    // largest split product of a left move: corner GEMM 3 / edge GEMM (chi^2 x D2^2 x D2^2, 8B),
+    // halves (N^3, 4B), M (N^3, 2B), projectors (N chi N, 2B), edge absorption (chi D2chi N, 2B)
+    const int D2 = c.D2, chi = c.chi, N = c.N;
+    size_t mx = 0;
+    const long long shapes[][4] = {{(long long)chi * chi, D2 * D2, D2 * D2, 8 * B},
+                                   {N, N, N, 4 * B}, {N, N, N, 2 * B}, {N, chi, N, 2 * B},
+                                   {chi, N, N, 2 * B}, {chi, (long long)D2 * chi, N, 2 * B},
+                                   {(long long)chi * D2, (long long)D2 * chi, chi, 8 * B}};
+    for (auto& sh : shapes) {
+      const size_t b = tc::split_workspace_bytes((int)sh[0], (int)sh[1], (int)sh[2], (int)sh[3]);
+      mx = b > mx ? b : mx;
+    }
+    c.tcwork_bytes = mx;
+    c.tcwork = a.take<unsigned char>(mx);
+  }
 }
 
 void ctm_build_plans(Ctx& c) {
@@ -283,17 +303,24 @@ __global__ void env_init_kernel(const cplx* a0A, const cplx* a0B, int B, int D, 
 
 // Projector factors from the SVD of M: rank K (multiplets at the cut kept whole, values below
 // cut_rel of the largest dropped), Vs = V[:, :K] S^{-1/2}, Us = U[:, :K] S^{-1/2}, zero-padded to chi.
+// Two values at the cut form a multiplet when their relative gap is below degen_rtol or their
+// absolute gap below degen_abs * s_1: a computed singular value is accurate to about eps * s_1, so
+// for small values a purely relative test would decide on rounding noise.
+constexpr double kDegenRtol = 1e-10, kDegenAbs = 1e-11, kTinyRel = 1e-14;
+
 __global__ void proj_prep_kernel(const double* S, long long s_stride, int ns, const cplx* U,
                                  const cplx* V, int N, int chi, long long ldu, long long stride_uv,
-                                 cplx* Us, cplx* Vs, int* kept, double degen_rtol, double tiny_rel,
-                                 double cut_rel) {
+                                 cplx* Us, cplx* Vs, int* kept, double degen_rtol, double degen_abs,
+                                 double tiny_rel, double cut_rel) {
   // S: ns singular values (descending) per problem; U, V: N x (>= chi) with leading dimension ldu
   const int q = blockIdx.x;
   const double* s = S + (size_t)q * s_stride;
   __shared__ int sK;
   if (threadIdx.x == 0) {
     int K = chi < ns ? chi : ns;
-    while (K > 1 && K < ns && s[K] > tiny_rel * s[0] && s[K - 1] / s[K] - 1.0 < degen_rtol) --K;
+    while (K > 1 && K < ns && s[K] > tiny_rel * s[0] &&
+           (s[K - 1] / s[K] - 1.0 < degen_rtol || s[K - 1] - s[K] < degen_abs * s[0]))
+      --K;
     int cnt = 0;
     for (int j = 0; j < K; ++j) cnt += s[j] > cut_rel * s[0];
     K = cnt < K ? cnt : K;
@@ -380,9 +407,16 @@ __global__ void normalize_store_kernel(const cplx* C1n, const cplx* T4n, const c
 }
 
 // Convergence number per instance: max over the 16 corners of || s/s_1 - s_prev/s_1,prev ||_2.
-// first != 0 only records the spectra of the starting environment.
+// first != 0 only records the spectra of the starting environment.  An instance is frozen (its
+// environment no longer updated) once delta < tol, or once delta has stalled at its rounding floor:
+// no factor-2 improvement of the best delta for kStallWindow sweeps while that best is below
+// kStallMax ("sufficiently well converged", Appendix).  tol <= 0 never freezes.
+constexpr int kStallWindow = 10;
+constexpr double kStallMax = 1e-7;
+
 __global__ void spectra_delta_kernel(const double* cs, double* prev, int B, int chi, int first,
-                                     double tol, double* delta, int* frozen, int* sweeps) {
+                                     double tol, double* delta, int* frozen, int* sweeps,
+                                     double* best, int* since) {
   const int b = blockIdx.x;
   __shared__ double dmax[16];
   const int c = threadIdx.x;
@@ -401,14 +435,28 @@ __global__ void spectra_delta_kernel(const double* cs, double* prev, int B, int 
     dmax[c] = sqrt(acc);
   }
   __syncthreads();
-  if (c == 0 && !first) {
-    double m = 0.0;
-    for (int k = 0; k < 16; ++k) m = fmax(m, dmax[k]);
-    if (!(m == m)) m = INFINITY;
-    delta[b] = m;
-    sweeps[b] += 1;
-    if (m < tol) frozen[b] = 1;
+  if (c != 0) return;
+  if (first) {
+    best[b] = INFINITY;
+    since[b] = 0;
+    return;
   }
+  double m = 0.0;
+  for (int k = 0; k < 16; ++k) m = fmax(m, dmax[k]);
+  if (!(m == m)) m = INFINITY;
+  delta[b] = m;
+  sweeps[b] += 1;
+  if (m < tol) {
+    frozen[b] = 1;
+    return;
+  }
+  if (m < 0.5 * best[b]) {
+    best[b] = m;
+    since[b] = 0;
+  } else {
+    since[b] += 1;
+  }
+  if (tol > 0.0 && since[b] >= kStallWindow && best[b] < kStallMax) frozen[b] = 1;
 }
 
 // ----------------------------------------------------------------------------- drivers
@@ -428,6 +476,16 @@ int ctm_init_env(Ctx& c) {
   for (int f = 0; f < 4; ++f)
     for (int x = 0; x < 2; ++x) c.slot_warm[f][x] = false;
   return 0;
+}
+
+// Contraction dispatcher: with precision = split BF16x3, products of at least kSplitMinWork complex
+// multiply-adds run on the tensor cores; everything else (and the FP64 path) uses the FP64 GEMM.
+constexpr double kSplitMinWork = 1 << 20;
+
+static int contract(Ctx& c, const GemmDesc& g) {
+  if (c.precision == 1 && (double)g.M * g.N * (double)g.K * g.batch >= kSplitMinWork && !g.skip)
+    return tc::zgemm_split_bf16(g, c.tcwork, c.tcwork_bytes, c.derr, c.st);
+  return zgemm_f64(g, c.st);
 }
 
 static GemmDesc gd(int M, int N, int K, int batch) {
@@ -473,7 +531,7 @@ __global__ void sub_refill_kernel(cplx* Z, int N, int k, unsigned long long seed
 // M v_j = s_j u_j holds by construction), the triplets are converged when M^+ u_j = s_j v_j too:
 // residual_j = || (M^+ U_y)_j - s_j (V_f)_j || <= rtol * s_1 for the first min(k, chi + 1) columns.
 __global__ void sub_residual_kernel(const cplx* Z, const cplx* Vf, const double* S, int N, int k,
-                                    int ncheck, double rtol, int* done, int* rounds) {
+                                    int ncheck, double rtol, int* done, int* rounds, double* prev) {
   const int q = blockIdx.x;
   if (done[q]) return;
   const cplx* Zq = Z + (size_t)q * N * k;
@@ -497,8 +555,12 @@ __global__ void sub_residual_kernel(const cplx* Z, const cplx* Vf, const double*
     __syncthreads();
   }
   if (threadIdx.x == 0) {
+    const double r = sqrt(worst);
+    // accepted at rtol, or once the residual stops shrinking (factor 2 per round) below 1e-10 s_1:
+    // then it sits at the rounding floor of the small directions
+    if (r <= rtol * s[0] || (rounds[q] > 0 && r <= 1e-10 * s[0] && r > 0.5 * prev[q])) done[q] = 1;
+    prev[q] = r;
     rounds[q] += 1;
-    if (sqrt(worst) <= rtol * s[0]) done[q] = 1;
   }
 }
 
@@ -548,7 +610,7 @@ static int subspace_svd(Ctx& c, int f, int x, const cplx* R, const cplx* Rt) {
     if ((rc = zgemm_f64(g, st))) return rc;
     IPEPS_LAUNCH(K_PROJ_PREP, 0, st,
                  sub_residual_kernel<<<2 * B, 256, 0, st>>>(w.Zsub, slot, w.Sy, N, k, ncheck, 1e-12,
-                                                            w.sub_done, w.sub_rounds));
+                                                            w.sub_done, w.sub_rounds, w.sub_res));
     if (it + 1 == rounds) break;
     IPEPS_LAUNCH(K_PROJ_PREP, 0, st,
                  sub_refill_kernel<<<2 * B, 256, 0, st>>>(w.Zsub, N, k, c.seed, stream_id * 1000 + it,
@@ -561,7 +623,7 @@ static int subspace_svd(Ctx& c, int f, int x, const cplx* R, const cplx* Rt) {
   c.slot_warm[f][x] = true;
   IPEPS_LAUNCH(K_PROJ_PREP, 0, st,
                proj_prep_kernel<<<2 * B, 256, 0, st>>>(w.Sy, k, k, w.Uy, slot, N, chi, k, Nk, w.Us,
-                                                       w.Vs, w.kept, 1e-10, 1e-14, c.cut_rel));
+                                                       w.Vs, w.kept, kDegenRtol, kDegenAbs, kTinyRel, c.cut_rel));
   return 0;
 }
 
@@ -576,10 +638,10 @@ static int left_move(Ctx& c, int f, int x) {
   // enlarged corners (8B problems)
   GemmDesc g = gd(chi, D2 * chi, chi, 8 * B);
   g.Aptr = m.g1A; g.Bptr = m.g1B; g.Cptr = m.g1C; g.lda = chi; g.ldb = D2 * chi; g.ldc = D2 * chi;
-  if ((rc = zgemm_f64(g, st))) return rc;
+  if ((rc = contract(c, g))) return rc;
   g = gd(chi * D2, D2 * chi, chi, 8 * B);
   g.Aptr = m.g2A; g.Bptr = m.g2B; g.Cptr = m.g2C; g.lda = chi; g.ldb = D2 * chi; g.ldc = D2 * chi;
-  if ((rc = zgemm_f64(g, st))) return rc;
+  if ((rc = contract(c, g))) return rc;
   {
     const int dims[4] = {chi, D2, D2, chi}, perm[4] = {0, 3, 2, 1};
     if ((rc = permute_c128(w.X2, w.X2p, 4, dims, perm, 8 * B, N2, N2, st))) return rc;
@@ -588,7 +650,7 @@ static int left_move(Ctx& c, int f, int x) {
   g.A = w.X2p; g.sA = N2; g.lda = D2 * D2;
   g.Bptr = m.g3B; g.ldb = D2 * D2;
   g.C = w.Y; g.sC = N2; g.ldc = D2 * D2;
-  if ((rc = zgemm_f64(g, st))) return rc;
+  if ((rc = contract(c, g))) return rc;
   {
     const int dims[4] = {chi, chi, D2, D2}, perm[4] = {0, 2, 1, 3};
     if ((rc = permute_c128(w.Y, w.Q, 4, dims, perm, 8 * B, N2, N2, st))) return rc;
@@ -596,12 +658,12 @@ static int left_move(Ctx& c, int f, int x) {
   // halves and the product over the cut
   g = gd(N, N, N, 4 * B);
   g.Aptr = m.hA; g.Bptr = m.hB; g.Cptr = m.hC; g.lda = N; g.ldb = N; g.ldc = N;
-  if ((rc = zgemm_f64(g, st))) return rc;
+  if ((rc = contract(c, g))) return rc;
   cplx* Rt = w.H;
   cplx* R = w.H + (size_t)2 * B * N2;
   g = gd(N, N, N, 2 * B);
   g.A = R; g.sA = N2; g.lda = N; g.B = Rt; g.sB = N2; g.ldb = N; g.C = w.M; g.sC = N2; g.ldc = N;
-  if ((rc = zgemm_f64(g, st))) return rc;
+  if ((rc = contract(c, g))) return rc;
   if (!c.subspace) {
     // projector SVD: full one-sided Jacobi of M
     SvdDesc sd;
@@ -611,25 +673,25 @@ static int left_move(Ctx& c, int f, int x) {
     if ((rc = jacobi_svd(sd, st))) return rc;
     IPEPS_LAUNCH(K_PROJ_PREP, 0, st,
                  proj_prep_kernel<<<2 * B, 256, 0, st>>>(w.S, N, N, w.U, w.V, N, chi, N, N2, w.Us,
-                                                         w.Vs, w.kept, 1e-10, 1e-14, c.cut_rel));
+                                                         w.Vs, w.kept, kDegenRtol, kDegenAbs, kTinyRel, c.cut_rel));
   } else {
     if ((rc = subspace_svd(c, f, x, R, Rt))) return rc;
   }
   g = gd(N, chi, N, 2 * B);     // P = R~ Vs
   g.A = Rt; g.sA = N2; g.lda = N; g.B = w.Vs; g.sB = Nc; g.ldb = chi; g.C = w.P; g.sC = Nc; g.ldc = chi;
-  if ((rc = zgemm_f64(g, st))) return rc;
+  if ((rc = contract(c, g))) return rc;
   g = gd(chi, N, N, 2 * B);     // P~ = Us^+ R
   g.opA = OP_C; g.A = w.Us; g.sA = Nc; g.lda = chi;
   g.B = R; g.sB = N2; g.ldb = N; g.C = w.Pt; g.sC = Nc; g.ldc = N;
-  if ((rc = zgemm_f64(g, st))) return rc;
+  if ((rc = contract(c, g))) return rc;
   // absorption: C1' = P~[y-1] (C1 T1)
   g = gd(chi, chi, N, 2 * B);
   g.Aptr = m.c1A; g.lda = N; g.Bptr = m.c1B; g.ldb = chi; g.C = w.C1n; g.sC = chi2; g.ldc = chi;
-  if ((rc = zgemm_f64(g, st))) return rc;
+  if ((rc = contract(c, g))) return rc;
   // T4' = P~[y] (T4 a) P[y-1]
   g = gd(chi * D2, D2 * chi, chi, 2 * B);
   g.Aptr = m.z1A; g.lda = chi; g.Bptr = m.z1B; g.ldb = D2 * chi; g.C = w.Z1; g.sC = N2; g.ldc = D2 * chi;
-  if ((rc = zgemm_f64(g, st))) return rc;
+  if ((rc = contract(c, g))) return rc;
   {
     const int dims[4] = {chi, D2, D2, chi}, perm[4] = {0, 3, 2, 1};
     if ((rc = permute_c128(w.Z1, w.Z1p, 4, dims, perm, 2 * B, N2, N2, st))) return rc;
@@ -637,7 +699,7 @@ static int left_move(Ctx& c, int f, int x) {
   g = gd(chi * chi, D2 * D2, D2 * D2, 2 * B);
   g.A = w.Z1p; g.sA = N2; g.lda = D2 * D2; g.Bptr = m.z2B; g.ldb = D2 * D2;
   g.C = w.Z2; g.sC = N2; g.ldc = D2 * D2;
-  if ((rc = zgemm_f64(g, st))) return rc;
+  if ((rc = contract(c, g))) return rc;
   {
     const int dims[4] = {chi, chi, D2, D2}, perm[4] = {0, 2, 3, 1};
     if ((rc = permute_c128(w.Z2, w.Z2p, 4, dims, perm, 2 * B, N2, N2, st))) return rc;
@@ -645,18 +707,18 @@ static int left_move(Ctx& c, int f, int x) {
   g = gd(chi, D2 * chi, N, 2 * B);
   g.Aptr = m.t4A; g.lda = N; g.B = w.Z2p; g.sB = N2; g.ldb = D2 * chi; g.C = w.T4n; g.sC = T;
   g.ldc = D2 * chi;
-  if ((rc = zgemm_f64(g, st))) return rc;
+  if ((rc = contract(c, g))) return rc;
   // C4' = (T3 C4) P[y]
   g = gd(chi * D2, chi, chi, 2 * B);
   g.Aptr = m.w1A; g.lda = chi; g.Bptr = m.w1B; g.ldb = chi; g.C = w.W1; g.sC = T; g.ldc = chi;
-  if ((rc = zgemm_f64(g, st))) return rc;
+  if ((rc = contract(c, g))) return rc;
   {
     const int dims[3] = {chi, D2, chi}, perm[3] = {0, 2, 1};
     if ((rc = permute_c128(w.W1, w.W1p, 3, dims, perm, 2 * B, T, T, st))) return rc;
   }
   g = gd(chi, chi, N, 2 * B);
   g.A = w.W1p; g.sA = T; g.lda = N; g.Bptr = m.c4B; g.ldb = chi; g.C = w.C4n; g.sC = chi2; g.ldc = chi;
-  if ((rc = zgemm_f64(g, st))) return rc;
+  if ((rc = contract(c, g))) return rc;
   IPEPS_LAUNCH(K_NORM_STORE, 0, st,
                normalize_store_kernel<<<3 * 2 * B, 256, 0, st>>>(w.C1n, w.T4n, w.C4n, B, chi2, T, m.sC1, m.sT4,
                                                                 m.sC4, w.frozen, c.derr));
@@ -679,7 +741,7 @@ int ctm_spectra(Ctx& c, double tol, int first) {
   if (int rc = jacobi_svd(sd, c.st)) return rc;
   IPEPS_LAUNCH(K_SPECTRA, 0, c.st,
                spectra_delta_kernel<<<c.B, 32, 0, c.st>>>(c.w.cs, c.w.prev, c.B, c.chi, first, tol, c.w.delta,
-                                                          c.w.frozen, c.w.sweeps));
+                                                          c.w.frozen, c.w.sweeps, c.w.best, c.w.since));
   IPEPS_CUDA_TRY(cudaGetLastError());
   return 0;
 }

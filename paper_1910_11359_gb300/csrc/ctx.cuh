@@ -52,6 +52,8 @@ struct CtmWork {
   int* frozen;                       // [B]
   int* sweeps;                       // [B]
   int* have_prev;                    // [1]
+  double* best;                      // [B] best delta so far (stall test)
+  int* since;                        // [B] sweeps without a factor-2 improvement of best
   const cplx* const* csA; double* const* csS;   // [16B] corner SVD operands
   // projector SVD operands [2B]
   const cplx* const* pA; cplx* const* pU; double* const* pS; cplx* const* pV;
@@ -64,6 +66,7 @@ struct CtmWork {
   double *Sy, *Sz;                   // [2B][k]
   int* sub_done;                     // [2B] converged flags of the subspace iteration
   int* sub_rounds;                   // [2B] rounds used (diagnostics)
+  double* sub_res;                   // [2B] previous residual (stagnation test)
   const cplx* const* yA; cplx* const* yU; double* const* yS; cplx* const* yV;   // Jacobi of Y
   const cplx* const* zA; cplx* const* zU; double* const* zS;                    // Jacobi of Z
 };
@@ -76,6 +79,8 @@ struct Ctx {
   bool slot_warm[4][2] = {{false, false}, {false, false}, {false, false}, {false, false}};
   double dt = 0.02;
   double cut_rel = 1e-10;  // CTMRG projector truncation (relative)
+  void* tcwork = nullptr;  // split-precision GEMM workspace (precision == 1)
+  size_t tcwork_bytes = 0;
   unsigned long long seed = 0;
   std::vector<double> J, V, h;
   cudaStream_t st = nullptr;

@@ -127,6 +127,7 @@ constexpr int JTHREADS = 256;
 struct JacobiArgs {
   SvdDesc d;
   int np, ra, rw;
+  int lpp;                     // lanes per pair in the dot-product phase (power of two, 4..32)
   unsigned long long* flops;   // algorithmic flop counter (dot products + applied rotations)
 };
 
@@ -134,6 +135,58 @@ struct JacobiArgs {
 // pair of the np (even) columns meets exactly once in np - 1 rounds.
 __device__ __forceinline__ int rr_pos(int i, int r, int np) {
   return i == 0 ? 0 : ((i - 1 + r) % (np - 1)) + 1;
+}
+
+__device__ __forceinline__ bool finite_bits(double x) {
+  return ((__double_as_longlong(x) >> 52) & 0x7FF) != 0x7FF;
+}
+
+// Rotation of one pair from its Gram entries al = |a_p|^2, be = |a_q|^2, gamma = a_p^+ a_q
+// (gr + i gi).  The update a_p <- c a_p - s e a_q, a_q <- s a_p + c e a_q zeroes gamma for
+// zeta = (be - al) / 2|gamma|, t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1 / sqrt(1 + t^2),
+// s = c t and e = conj(gamma) / |gamma|.
+// FP64 issue is slow on this part, so the fast path forms t in FP32 (the angle only steers the
+// iteration; a relative error of 1e-7 in t leaves an off-diagonal of ~1e-7 |gamma| that the next
+// sweep removes) while c, s and e are formed in FP64 from that t, so the applied transformation
+// is unitary to FP64 rounding.  Column norms outside [1e-70, 1e70] or extreme zeta take the
+// all-FP64 path.  Returns 1 when the pair is rotated.
+__device__ __forceinline__ int jacobi_rotation(double al, double be, double gr, double gi, double tol,
+                                               double* out) {
+  const double g2 = fma(gr, gr, gi * gi);
+  if (al > 1e-140 && al < 1e140 && be > 1e-140 && be < 1e140) {
+    if (!(g2 > tol * tol * (al * be))) return 0;
+    const double rg = rsqrt(g2);
+    const double zeta = (be - al) * (0.5 * rg);
+    if (fabs(zeta) < 1e30) {
+      const float zf = (float)zeta, az = fabsf(zf);
+      const float tf = az > 1e4f ? 0.5f / zf : copysignf(1.0f, zf) / (az + sqrtf(fmaf(zf, zf, 1.0f)));
+      const double t = (double)tf;
+      const double c = rsqrt(fma(t, t, 1.0));
+      out[0] = c;
+      out[1] = c * t;
+      out[2] = gr * rg;
+      out[3] = -gi * rg;
+      return 1;
+    }
+  }
+  // all-FP64 path: rescaled phase, exact angle
+  const double g = sqrt(g2 > 0.0 ? g2 : 0.0);
+  if (!(al > JTINY && be > JTINY)) return 0;
+  const double mg = fmax(fabs(gr), fabs(gi));
+  if (!(mg > 0.0)) return 0;
+  const double grs = gr / mg, gis = gi / mg;
+  const double gn = sqrt(grs * grs + gis * gis);
+  const double gabs = mg * gn;                      // |gamma| without underflow
+  if (!(gabs > tol * sqrt(al) * sqrt(be))) return 0;
+  (void)g;
+  const double zeta = (be - al) / (2.0 * gabs);
+  const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + hypot(1.0, zeta));
+  const double c = 1.0 / sqrt(1.0 + t * t);
+  out[0] = c;
+  out[1] = c * t;
+  out[2] = grs / gn;
+  out[3] = -gis / gn;
+  return 1;
 }
 
 __global__ void __cluster_dims__(JCS, 1, 1) __launch_bounds__(JTHREADS)
@@ -152,8 +205,8 @@ jacobi_kernel(JacobiArgs args) {
   extern __shared__ __align__(16) unsigned char jsm_raw[];
   cplx* colA = reinterpret_cast<cplx*>(jsm_raw);           // colA[j * ra + i]
   cplx* colW = colA + (size_t)np * ra;                      // colW[j * rw + i]
-  double* part = reinterpret_cast<double*>(colW + (size_t)np * rw);   // [2][npairs][4]
-  double* rot = part + 2 * npairs * 4;                      // [npairs][4]: c, s, er, ei
+  double* part = reinterpret_cast<double*>(colW + (size_t)np * rw);   // [2][JCS][npairs][4]
+  double* rot = part + 2 * JCS * npairs * 4;                // [npairs][4]: c, s, er, ei
   int* flags = reinterpret_cast<int*>(rot + npairs * 4);    // [npairs] + any + nonfinite
 
   const cplx* A = d.A[prob];
@@ -170,71 +223,82 @@ jacobi_kernel(JacobiArgs args) {
   __syncthreads();
 
   const int nrounds = np - 1;
+  const int lpp = args.lpp, ppw = 32 / lpp;                 // dot phase: lpp lanes per pair
+  const int sub = lane & (lpp - 1), slot = lane / lpp;
   long long gcount = 0;
   __shared__ int nrot_round;
-  double work = 0.0;   // flops of this problem, tallied by rank 0 / thread 0
+  long long nrot_total = 0;    // rotations applied (tallied by thread 0)
   int sweep = 0;
   bool converged = false;
   for (sweep = 0; sweep < d.max_sweeps; ++sweep) {
     for (int r = 0; r < nrounds; ++r, ++gcount) {
       const int buf = (int)(gcount & 1);
-      double* mypart = part + buf * npairs * 4;
-      for (int p = warp; p < npairs; p += nwarps) {
-        const int cp = rr_pos(p, r, np), cq = rr_pos(np - 1 - p, r, np);
+      // slot of this CTA's partial sums inside every CTA's buffer
+      const size_t myslot = ((size_t)buf * JCS + rank) * npairs * 4;
+      // dot products: ppw pairs per warp, lpp lanes per pair, reduced by shuffles within the group
+      for (int pb = warp * ppw; pb < npairs; pb += nwarps * ppw) {
+        const int p = pb + slot;
+        const bool valid = p < npairs;
         double al = 0.0, be = 0.0, gr = 0.0, gi = 0.0;
-        for (int i = lane; i < ra; i += 32) {
-          cplx x = colA[cp * ra + i], y = colA[cq * ra + i];
-          al = fma(x.x, x.x, fma(x.y, x.y, al));
-          be = fma(y.x, y.x, fma(y.y, y.y, be));
-          gr = fma(x.x, y.x, fma(x.y, y.y, gr));
-          gi = fma(x.x, y.y, fma(-x.y, y.x, gi));
+        if (valid) {
+          const int cp = rr_pos(p, r, np), cq = rr_pos(np - 1 - p, r, np);
+          for (int i = sub; i < ra; i += lpp) {
+            cplx x = colA[cp * ra + i], y = colA[cq * ra + i];
+            al = fma(x.x, x.x, fma(x.y, x.y, al));
+            be = fma(y.x, y.x, fma(y.y, y.y, be));
+            gr = fma(x.x, y.x, fma(x.y, y.y, gr));
+            gi = fma(x.x, y.y, fma(-x.y, y.x, gi));
+          }
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
+        for (int o = lpp >> 1; o > 0; o >>= 1) {
           al += __shfl_xor_sync(0xffffffffu, al, o);
           be += __shfl_xor_sync(0xffffffffu, be, o);
           gr += __shfl_xor_sync(0xffffffffu, gr, o);
           gi += __shfl_xor_sync(0xffffffffu, gi, o);
         }
-        if (lane == 0) {
-          mypart[p * 4 + 0] = al; mypart[p * 4 + 1] = be;
-          mypart[p * 4 + 2] = gr; mypart[p * 4 + 3] = gi;
-        }
+        // push the partials into every CTA of the cluster (remote stores do not stall; the
+        // cluster barrier below makes them visible), so the reduction reads only local memory
+        if (valid)
+          for (int q = sub; q < JCS; q += lpp) {
+            double* dst = cluster.map_shared_rank(part, q) + myslot + p * 4;
+            dst[0] = al; dst[1] = be; dst[2] = gr; dst[3] = gi;
+          }
       }
       if (tid == 0) nrot_round = 0;
       cluster.sync();
-      // every CTA sums the partials in rank order, so all CTAs reach bit-identical decisions
-      for (int p = tid; p < npairs; p += JTHREADS) {
-        double al = 0.0, be = 0.0, gr = 0.0, gi = 0.0;
-        for (int q = 0; q < JCS; ++q) {
-          const double* rp = cluster.map_shared_rank(part, q) + buf * npairs * 4 + p * 4;
-          al += rp[0]; be += rp[1]; gr += rp[2]; gi += rp[3];
+      // decisions: 4 lanes per pair, one Gram component each summed over the CTAs in rank order
+      // (so every CTA reaches bit-identical decisions), then gathered by shuffles
+      for (int pb = warp * 8; pb < npairs; pb += nwarps * 8) {
+        const int p = pb + (lane >> 2), comp = lane & 3;
+        double acc = 0.0;
+        if (p < npairs)
+          for (int q = 0; q < JCS; ++q) acc += part[((size_t)buf * JCS + q) * npairs * 4 + p * 4 + comp];
+        const int base = lane & ~3;
+        const double al = __shfl_sync(0xffffffffu, acc, base);
+        const double be = __shfl_sync(0xffffffffu, acc, base + 1);
+        const double gr = __shfl_sync(0xffffffffu, acc, base + 2);
+        const double gi = __shfl_sync(0xffffffffu, acc, base + 3);
+        if (p < npairs && comp == 0) {
+          int doit = 0;
+          if (!(finite_bits(al) && finite_bits(be) && finite_bits(gr) && finite_bits(gi))) {
+            flags[npairs + 1] = 1;
+          } else {
+            double rr[4];
+            doit = jacobi_rotation(al, be, gr, gi, d.tol, rr);
+            if (doit) {
+              rot[p * 4 + 0] = rr[0];
+              rot[p * 4 + 1] = rr[1];
+              rot[p * 4 + 2] = rr[2];
+              rot[p * 4 + 3] = rr[3];
+              flags[npairs] = 1;
+              atomicAdd(&nrot_round, 1);
+            }
+          }
+          flags[p] = doit;
         }
-        const double g = sqrt(gr * gr + gi * gi);
-        int doit = 0;
-        if (!(isfinite(al) && isfinite(be) && isfinite(g))) {
-          flags[npairs + 1] = 1;
-        } else if (al > JTINY && be > JTINY && g > d.tol * sqrt(al) * sqrt(be)) {
-          const double zeta = (be - al) / (2.0 * g);
-          const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + hypot(1.0, zeta));
-          const double c = 1.0 / sqrt(1.0 + t * t);
-          // phase conj(gamma)/|gamma| from the rescaled components (no precision loss when the
-          // components of gamma are small)
-          const double mg = fmax(fabs(gr), fabs(gi));
-          const double grs = gr / mg, gis = gi / mg;
-          const double gn = sqrt(grs * grs + gis * gis);
-          rot[p * 4 + 0] = c;
-          rot[p * 4 + 1] = c * t;
-          rot[p * 4 + 2] = grs / gn;
-          rot[p * 4 + 3] = -gis / gn;
-          doit = 1;
-          flags[npairs] = 1;
-          atomicAdd(&nrot_round, 1);
-        }
-        flags[p] = doit;
       }
       __syncthreads();
-      if (tid == 0) work += 16.0 * m * npairs + 14.0 * (m + n) * nrot_round;
+      if (tid == 0) nrot_total += nrot_round;
       if (flags[npairs + 1]) break;
       const int rows = ra + rw;
       for (int idx = tid; idx < npairs * rows; idx += JTHREADS) {
@@ -311,7 +375,10 @@ jacobi_kernel(JacobiArgs args) {
     }
   }
   if (tid == 0 && rank == 0) {
-    if (args.flops) atomicAdd(args.flops, (unsigned long long)work);
+    if (args.flops) {
+      const double work = 16.0 * m * npairs * (double)gcount + 14.0 * (m + n) * (double)nrot_total;
+      atomicAdd(args.flops, (unsigned long long)work);
+    }
     if (d.sweeps_out) d.sweeps_out[prob] = sweep + 1;
     if (d.err) {
       if (nonfinite_any) atomicOr(d.err, (unsigned)DEV_NONFINITE);
@@ -331,7 +398,7 @@ size_t jacobi_svd_smem_bytes(int m, int n) {
   int np, ra, rw;
   jacobi_layout(m, n, &np, &ra, &rw);
   size_t npairs = np / 2;
-  return (size_t)np * (ra + rw) * sizeof(cplx) + (2 * npairs * 4 + npairs * 4) * sizeof(double) +
+  return (size_t)np * (ra + rw) * sizeof(cplx) + (2 * JCS * npairs * 4 + npairs * 4) * sizeof(double) +
          (npairs + 2 + np) * sizeof(int) + 64;
 }
 
@@ -354,6 +421,9 @@ int jacobi_svd(const SvdDesc& d, cudaStream_t st) {
     attr_set = true;
   }
   a.flops = prof_device_flops();
+  // dot-product lanes per pair: about 4 rows per lane, 4..32 lanes
+  a.lpp = 4;
+  while (a.lpp < 32 && a.lpp * 4 < a.ra) a.lpp *= 2;
   IPEPS_LAUNCH(K_JACOBI, 0, st, jacobi_kernel<<<d.batch * JCS, JTHREADS, smem, st>>>(a));
   IPEPS_CUDA_TRY(cudaGetLastError());
   return 0;

@@ -1,0 +1,425 @@
+// Split-precision complex GEMM on the tcgen05 tensor cores (sm_103a).
+//
+// A complex product C = op(A) op(B) (M x K times K x N) becomes one real GEMM on the embedding
+//   A_big = [[Ar, -Ai], [Ai, Ar]]  (2M x 2K),   B_big = [Br; Bi]  (2K x N),   C_big = [Cr; Ci],
+// and each FP64 value x is split into two BF16 terms x ~ hi + lo (hi = bf16(x), lo = bf16(x - hi));
+// the three leading products hi*hi + hi*lo + lo*hi are obtained by tripling K:
+//   A3 = [A_hi | A_hi | A_lo],  B3 = [B_hi ; B_lo ; B_hi]   (K3 = 6K),  C_big = A3 B3,
+// accumulated in FP32.  Operands are prepared K-major (A3 rows x K3, B3^T rows x K3) by elementwise
+// kernels; the GEMM kernel below is a plain BF16 x BF16 -> FP32 tcgen05 GEMM:
+//   * one CTA per 128 x 128 output tile, 6 warps: warp 0 issues TMA loads (128B-swizzled 128 x 64
+//     tiles of both operands into a 4-stage ring), warp 1 allocates 128 TMEM columns and one of its
+//     threads issues tcgen05.mma (M = 128, N = 128, K = 16, BF16 in, FP32 accumulator in TMEM),
+//     warps 2..5 read the accumulator with tcgen05.ld and store FP32 rows;
+//   * full / empty mbarriers per stage (TMA transaction bytes / tcgen05.commit), one more for the
+//     finished accumulator; every wait is bounded: on timeout the CTA raises DEV_TIMEOUT in the
+//     error word, the other roles stop, outstanding TMA loads are drained (bounded) and the TMEM
+//     columns are released before the CTA exits.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <mutex>
+
+#include "prof.cuh"
+#include "tc_gemm.cuh"
+
+namespace ipeps {
+namespace tc {
+
+constexpr int BM = 128, BK = 64, STAGES = 4, THREADS = 192;
+constexpr uint32_t A_BYTES = BM * BK * 2;                  // 16 KB A tile per stage
+// per output-tile width BN (128 or 256): B tile bytes, shared memory, TMEM columns
+template <int BN> struct TileCfg {
+  static constexpr uint32_t B_BYTES = BN * BK * 2;
+  static constexpr uint32_t SMEM_BYTES = STAGES * (A_BYTES + B_BYTES) + 1024 + 256;
+  static constexpr uint32_t TMEM_COLS = BN;
+  // instruction descriptor, kind::f16: BF16 A and B (K-major), FP32 accumulator, M = 128, N = BN
+  static constexpr uint32_t IDESC = (1u << 4)        // D format F32
+                                    | (1u << 7)      // A format BF16
+                                    | (1u << 10)     // B format BF16
+                                    | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+};
+constexpr long long SPIN_LIMIT = 1LL << 24;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait; returns false on timeout or when another role has aborted
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+  for (long long it = 0; it < SPIN_LIMIT; ++it) {
+    if (mbar_try(bar, parity)) return true;
+    if ((it & 255) == 255 && *abort_flag) return false;
+  }
+  return false;
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x,
+                                            int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
+// shared-memory matrix descriptor: K-major operand tile written by TMA with 128-byte swizzle,
+// rows of 128 bytes, 8-row core-matrix groups 1024 bytes apart (tile base 1024-byte aligned)
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;                  // leading-dimension byte offset (unused for this layout)
+  d |= (uint64_t)(1024 >> 4) << 32;        // stride byte offset: next 8-row group
+  d |= (uint64_t)1 << 46;                  // descriptor version (sm_100 family)
+  d |= (uint64_t)2 << 61;                  // 128-byte swizzle
+  return d;
+}
+template <int BN>
+__global__ void __launch_bounds__(THREADS, 1)
+tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+               float* __restrict__ C, long long ldc, long long strideC, int ktiles, unsigned* err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  unsigned char* smem = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
+  const uint32_t sA = smem_u32(smem);
+  using Cfg = TileCfg<BN>;
+  const uint32_t sB = sA + STAGES * A_BYTES;
+  unsigned char* tail = smem + STAGES * (A_BYTES + Cfg::B_BYTES);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(tail);       // full[STAGES], empty[STAGES], done
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tail + 8 * (2 * STAGES + 1));
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * STAGES, done_bar = full0 + 16 * STAGES;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM, bz = blockIdx.z;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    mbar_init(done_bar, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(Cfg::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer
+    int issued = 0;
+    for (int kt = 0; kt < ktiles; ++kt) {
+      const int s = kt % STAGES;
+      const uint32_t ph = (uint32_t)(kt / STAGES) & 1u;
+      if (!mbar_wait(empty0 + 8 * s, ph ^ 1u, abort_flag)) {
+        *abort_flag = 1;
+        atomicOr(err, (unsigned)DEV_TIMEOUT);
+        break;
+      }
+      mbar_expect_tx(full0 + 8 * s, A_BYTES + Cfg::B_BYTES);
+      tma_load_3d(sA + s * A_BYTES, &tmA, full0 + 8 * s, kt * BK, m0, bz);
+      tma_load_3d(sB + s * Cfg::B_BYTES, &tmB, full0 + 8 * s, kt * BK, n0, bz);
+      ++issued;
+    }
+    // drain: every issued load has completed before the CTA may exit (bounded)
+    for (int kt = issued > STAGES ? issued - STAGES : 0; kt < issued; ++kt) {
+      const int s = kt % STAGES;
+      const uint32_t ph = (uint32_t)(kt / STAGES) & 1u;
+      for (long long it = 0; it < SPIN_LIMIT && !mbar_try(full0 + 8 * s, ph); ++it) {
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    bool ok = true;
+    for (int kt = 0; kt < ktiles; ++kt) {
+      const int s = kt % STAGES;
+      const uint32_t ph = (uint32_t)(kt / STAGES) & 1u;
+      if (!mbar_wait(full0 + 8 * s, ph, abort_flag)) {
+        *abort_flag = 1;
+        atomicOr(err, (unsigned)DEV_TIMEOUT);
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint64_t da = smem_desc(sA + s * A_BYTES), db = smem_desc(sB + s * Cfg::B_BYTES);
+#pragma unroll
+      for (int k = 0; k < BK / 16; ++k) {
+        const uint32_t acc = (kt > 0 || k > 0) ? 1u : 0u;
+        const uint64_t adv = (uint64_t)((k * 32) >> 4);   // 16 BF16 = 32 bytes along K
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(da + adv), "l"(db + adv), "r"(Cfg::IDESC), "r"(acc)
+            : "memory");
+      }
+      // the stage is free once these MMAs have read it
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       empty0 + 8 * s)
+                   : "memory");
+    }
+    (void)ok;
+    // accumulator complete (also signalled after an abort, so the epilogue never waits forever)
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     done_bar)
+                 : "memory");
+  } else if (warp >= 2) {
+    // ---------------- epilogue: TMEM lanes (32 q .. 32 q + 31) of warp quarter q = warp % 4
+    const int q = warp & 3;
+    bool ok = mbar_wait(done_bar, 0, abort_flag);
+    if (!ok && lane == 0) {
+      *abort_flag = 1;
+      atomicOr(err, (unsigned)DEV_TIMEOUT);
+    }
+    // warp-uniform decision: tcgen05.ld is .sync.aligned
+    ok = __all_sync(0xffffffffu, ok && !*abort_flag);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+      const int row = m0 + 32 * q + lane;
+      float* crow = C + (long long)bz * strideC + (long long)row * ldc + n0;
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        uint32_t r[32];
+        const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+            "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+            "%28, %29, %30, %31}, [%32];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+              "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+              "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+              "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+              "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+              "=r"(r[31])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        float4* dst = reinterpret_cast<float4*>(crow + c0);
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          dst[j] = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
+                               __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    // after an abort the issued MMAs may still be running: wait (bounded) for their commit before
+    // the columns are released; on the normal path this phase has already completed
+    if (lane == 0)
+      for (long long it = 0; it < SPIN_LIMIT && !mbar_try(done_bar, 0); ++it) {
+      }
+    __syncwarp();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Cfg::TMEM_COLS)
+                 : "memory");
+  }
+}
+
+// ----------------------------------------------------------------------------- operand preparation
+__device__ __forceinline__ void split_bf16(double x, __nv_bfloat16* hi, __nv_bfloat16* lo) {
+  const __nv_bfloat16 h = __float2bfloat16_rn((float)x);
+  *hi = h;
+  *lo = __float2bfloat16_rn((float)(x - (double)__bfloat162float(h)));
+}
+
+// element (row, col) of op(P) for a complex operand stored with leading dimension ld
+__device__ __forceinline__ cplx op_elem(const cplx* P, long long ld, int op, int row, int col) {
+  if (op == OP_N) return P[(long long)row * ld + col];
+  const cplx v = P[(long long)col * ld + row];
+  return op == OP_C ? cconj(v) : v;
+}
+
+// A3[b][i][c], i < Mp (2M real rows, zero beyond), c < Kp (6K used):
+//   segment c / 2K: 0, 1 -> hi part, 2 -> lo part of A_big[i][c % 2K]
+__global__ void prep_a_kernel(GemmDesc g, __nv_bfloat16* A3, int Mp, int Kp) {
+  const int M = g.M, K = g.K;
+  const long long per = (long long)Mp * Kp;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < per * g.batch;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(idx / per);
+    const int i = (int)((idx % per) / Kp), c = (int)(idx % Kp);
+    __nv_bfloat16 out = __float2bfloat16_rn(0.f);
+    if (i < 2 * M && c < 6 * K) {
+      const int seg = c / (2 * K), cc = c % (2 * K);
+      const cplx* A = g.Aptr ? g.Aptr[b] : g.A + (long long)b * g.sA;
+      const int r = i < M ? i : i - M;
+      const cplx v = op_elem(A, g.lda, g.opA, r, cc < K ? cc : cc - K);
+      double x;
+      if (i < M) x = cc < K ? v.x : -v.y;      // [Ar, -Ai]
+      else x = cc < K ? v.y : v.x;             // [Ai,  Ar]
+      __nv_bfloat16 hi, lo;
+      split_bf16(x, &hi, &lo);
+      out = seg == 2 ? lo : hi;
+    }
+    A3[idx] = out;
+  }
+}
+
+// B3t[b][j][c], j < Np (N used), c < Kp: segment 0, 2 -> hi, 1 -> lo of B_big[c % 2K][j]
+__global__ void prep_b_kernel(GemmDesc g, __nv_bfloat16* B3t, int Np, int Kp) {
+  const int N = g.N, K = g.K;
+  const long long per = (long long)Np * Kp;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < per * g.batch;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(idx / per);
+    const int j = (int)((idx % per) / Kp), c = (int)(idx % Kp);
+    __nv_bfloat16 out = __float2bfloat16_rn(0.f);
+    if (j < N && c < 6 * K) {
+      const int seg = c / (2 * K), cc = c % (2 * K);
+      const cplx* B = g.Bptr ? g.Bptr[b] : g.B + (long long)b * g.sB;
+      const cplx v = op_elem(B, g.ldb, g.opB, cc < K ? cc : cc - K, j);
+      const double x = cc < K ? v.x : v.y;     // [Br; Bi]
+      __nv_bfloat16 hi, lo;
+      split_bf16(x, &hi, &lo);
+      out = seg == 1 ? lo : hi;
+    }
+    B3t[idx] = out;
+  }
+}
+
+// C[b][i][j] = alpha (C32[i][j] + i C32[M + i][j]) + beta C[b][i][j]
+__global__ void gather_c_kernel(GemmDesc g, const float* C32, int Mp, int Np) {
+  const int M = g.M, N = g.N;
+  const long long per = (long long)M * N;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < per * g.batch;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(idx / per);
+    const int i = (int)((idx % per) / N), j = (int)(idx % N);
+    const float* cb = C32 + (long long)b * Mp * Np;
+    cplx v = cmk((double)cb[(long long)i * Np + j], (double)cb[(long long)(M + i) * Np + j]);
+    cplx* Cb = g.Cptr ? g.Cptr[b] : g.C + (long long)b * g.sC;
+    const long long o = (long long)i * g.ldc + j;
+    cplx r = cmul(g.alpha, v);
+    if (g.beta.x != 0.0 || g.beta.y != 0.0) r = cadd(r, cmul(g.beta, Cb[o]));
+    Cb[o] = r;
+  }
+}
+
+// ----------------------------------------------------------------------------- host side
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+static std::mutex g_encode_mu;
+
+static int encoder(PFN_cuTensorMapEncodeTiled_v12000* out) {
+  std::lock_guard<std::mutex> lk(g_encode_mu);
+  if (!g_encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                     cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+      return cuda_fail(e != cudaSuccess ? e : cudaErrorNotSupported, "cuTensorMapEncodeTiled lookup",
+                       __FILE__, __LINE__);
+    g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  }
+  *out = g_encode;
+  return 0;
+}
+
+// 3-D map over [batch][rows][Kp] BF16 with a (64 x box_rows x 1) box, 128-byte swizzle
+static int make_map(CUtensorMap* map, const void* base, int rows, int Kp, int batch, int box_rows) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc;
+  if (int rc = encoder(&enc)) return rc;
+  cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)batch};
+  cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)rows * Kp * 2};
+  cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides,
+                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cuda_fail(cudaErrorInvalidValue, "cuTensorMapEncodeTiled", __FILE__, __LINE__);
+  return 0;
+}
+
+static inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+// output-tile width: 256 (twice the reuse of each A tile) when that still gives every SM a tile
+static int pick_bn(int M, int N, int batch) {
+  const long long tiles256 = (long long)(round_up(2 * M, BM) / BM) * (round_up(N, 256) / 256) * batch;
+  return (N > 128 && tiles256 >= 152) ? 256 : 128;
+}
+
+size_t split_workspace_bytes(int M, int N, int K, int batch) {
+  const size_t Mp = round_up(2 * M, BM), Np = round_up(N, 256), Kp = round_up(6 * K, BK);
+  return (Mp * Kp + Np * Kp) * 2 * batch + Mp * Np * 4 * batch + 3 * 1024;
+}
+
+template <int BN>
+static int launch_tc(const CUtensorMap& mA, const CUtensorMap& mB, float* C32, int Mp, int Np, int Kp,
+                     int batch, unsigned* err, cudaStream_t st) {
+  using Cfg = TileCfg<BN>;
+  static bool attr = false;
+  if (!attr) {
+    IPEPS_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)Cfg::SMEM_BYTES));
+    attr = true;
+  }
+  dim3 grid(Np / BN, Mp / BM, batch);
+  const double flops = 2.0 * Mp * (double)Np * Kp * batch;
+  IPEPS_LAUNCH(K_TC_GEMM, flops, st,
+               tc_gemm_kernel<BN><<<grid, THREADS, Cfg::SMEM_BYTES, st>>>(mA, mB, C32, Np, (long long)Mp * Np,
+                                                                        Kp / BK, err));
+  IPEPS_CUDA_TRY(cudaGetLastError());
+  return 0;
+}
+
+int gemm_bf16_raw(const void* A3, const void* B3t, float* C32, int Mp, int Np, int Kp, int batch,
+                  int bn, unsigned* err, cudaStream_t st) {
+  if ((bn != 128 && bn != 256) || Mp % BM || Np % bn || Kp % BK || batch < 1 || batch > 65535)
+    return cuda_fail(cudaErrorInvalidValue, "tc gemm shape", __FILE__, __LINE__);
+  if (((uintptr_t)A3 & 15) || ((uintptr_t)B3t & 15) || ((uintptr_t)C32 & 15))
+    return cuda_fail(cudaErrorInvalidValue, "tc gemm alignment", __FILE__, __LINE__);
+  CUtensorMap mA, mB;
+  if (int rc = make_map(&mA, A3, Mp, Kp, batch, BM)) return rc;
+  if (int rc = make_map(&mB, B3t, Np, Kp, batch, bn)) return rc;
+  return bn == 256 ? launch_tc<256>(mA, mB, C32, Mp, Np, Kp, batch, err, st)
+                   : launch_tc<128>(mA, mB, C32, Mp, Np, Kp, batch, err, st);
+}
+
+int zgemm_split_bf16(const GemmDesc& g, void* work, size_t work_bytes, unsigned* err, cudaStream_t st) {
+  if (g.M <= 0 || g.N <= 0 || g.K <= 0 || g.batch <= 0) return 0;
+  const int bn = pick_bn(g.M, g.N, g.batch);
+  const int Mp = round_up(2 * g.M, BM), Np = round_up(g.N, bn), Kp = round_up(6 * g.K, BK);
+  if (split_workspace_bytes(g.M, g.N, g.K, g.batch) > work_bytes)
+    return cuda_fail(cudaErrorInvalidValue, "split workspace too small", __FILE__, __LINE__);
+  char* w = (char*)(((uintptr_t)work + 1023) & ~(uintptr_t)1023);
+  __nv_bfloat16* A3 = (__nv_bfloat16*)w;
+  w += ((size_t)Mp * Kp * 2 * g.batch + 1023) & ~(size_t)1023;
+  __nv_bfloat16* B3 = (__nv_bfloat16*)w;
+  w += ((size_t)Np * Kp * 2 * g.batch + 1023) & ~(size_t)1023;
+  float* C32 = (float*)w;
+  const int blocks = 152 * 8;
+  IPEPS_LAUNCH(K_TC_PREP, 0, st, prep_a_kernel<<<blocks, 256, 0, st>>>(g, A3, Mp, Kp));
+  IPEPS_LAUNCH(K_TC_PREP, 0, st, prep_b_kernel<<<blocks, 256, 0, st>>>(g, B3, Np, Kp));
+  IPEPS_CUDA_TRY(cudaGetLastError());
+  if (int rc = gemm_bf16_raw(A3, B3, C32, Mp, Np, Kp, g.batch, bn, err, st)) return rc;
+  IPEPS_LAUNCH(K_TC_PREP, 0, st, gather_c_kernel<<<blocks, 256, 0, st>>>(g, C32, Mp, Np));
+  IPEPS_CUDA_TRY(cudaGetLastError());
+  return 0;
+}
+
+}  // namespace tc
+}  // namespace ipeps
