@@ -47,7 +47,7 @@ import functools
 
 import numpy as np
 
-from .su import truncation_rank
+from .su import DEGEN_RTOL, TINY_REL, truncation_rank
 
 # every contraction below is a pairwise (or three-operand) einsum; optimize=True lets NumPy hand
 # each pairwise step to BLAS and changes nothing but speed
@@ -195,12 +195,38 @@ def corner_q4(T3, C4, T4, a):
 
 
 # ----------------------------------------------------------------------------- projectors
-def projectors(R, Rt, chi, cut_rel=PROJ_CUT_REL):
+def cut_margin(s, chi, cut_rel=PROJ_CUT_REL, degen_rtol=DEGEN_RTOL, degen_abs=PROJ_DEGEN_ABS):
+    """How far, in decades, the multiplet decisions at the chi cut lie from their thresholds.
+
+    For every pair (s[K-1], s[K]) the multiplet rule examines while it moves the cut down, with
+    s[K] above the cutoff (below it the cutoff decides anyway), the decision is "relative gap <
+    degen_rtol or absolute gap < degen_abs * s_1"; its margin is |log10| of the ratio of the deciding
+    threshold to the gap.  Returns the smallest margin (inf when no such pair exists).  A small
+    margin means the decision can go either way under rounding (C8)."""
+    m = np.inf
+    K = min(chi, len(s))
+    if not s[0] > 0:
+        return m
+    while 1 < K < len(s) and s[K] > max(TINY_REL, cut_rel) * s[0]:
+        rel = max(s[K - 1] / s[K] - 1.0, 1e-300)
+        ab = max((s[K - 1] - s[K]) / s[0], 1e-300)
+        d = max(np.log10(degen_rtol / rel), np.log10(degen_abs / ab))   # > 0: multiplet
+        m = min(m, abs(d))
+        if d <= 0:
+            break
+        K -= 1
+    return m
+
+
+def projectors(R, Rt, chi, cut_rel=PROJ_CUT_REL, log=None):
     """Full-SVD projectors for the bond joining R (columns) and R~ (rows); returns (P, P~, s).
 
-    s is the full singular spectrum of M = R R~ (for diagnostics)."""
+    s is the full singular spectrum of M = R R~ (for diagnostics).  When ``log`` is a list it
+    receives cut_margin() of this cut."""
     M = R @ Rt
     U, s, Vh = np.linalg.svd(M)
+    if log is not None:
+        log.append(cut_margin(s, chi, cut_rel))
     K = truncation_rank(s, chi, degen_abs=PROJ_DEGEN_ABS)
     K = min(K, int(np.sum(s > cut_rel * s[0]))) if s[0] > 0 else 0
     K = max(K, 1) if s[0] > 0 else 0
@@ -219,7 +245,7 @@ def _normalize(t):
     return t / m if m > 0 else t
 
 
-def left_move(a, env, x, chi, cut_rel=PROJ_CUT_REL):
+def left_move(a, env, x, chi, cut_rel=PROJ_CUT_REL, log=None):
     """Absorb column x into the left environment of column x+1 (all rows)."""
     Lx, Ly = env.Lx, env.Ly
     C, T = env.C, env.T
@@ -234,7 +260,7 @@ def left_move(a, env, x, chi, cut_rel=PROJ_CUT_REL):
         q4 = corner_q4(T[2][(x, yp)], C[3][(x, yp)], T[3][(x, yp)], a[(x, yp)])
         R = q3 @ q4       # rows: bond Q2|Q3, columns: the cut (bond Q4|Q1)
         Rt = q1 @ q2      # rows: the cut, columns: bond Q2|Q3
-        P[y], Pt[y], _ = projectors(R, Rt, chi, cut_rel)
+        P[y], Pt[y], _ = projectors(R, Rt, chi, cut_rel, log)
     newC1, newT4, newC4 = {}, {}, {}
     for y in range(Ly):
         ym = (y - 1) % Ly
@@ -250,11 +276,12 @@ def left_move(a, env, x, chi, cut_rel=PROJ_CUT_REL):
         C[3][(xp, y)] = _normalize(newC4[y])
 
 
-def sweep(a, env, chi, cut_rel=PROJ_CUT_REL):
-    """One CTMRG sweep: left, top, right and bottom moves, each over every column."""
+def sweep(a, env, chi, cut_rel=PROJ_CUT_REL, log=None):
+    """One CTMRG sweep: left, top, right and bottom moves, each over every column (16 projector
+    computations on the 2x2 cell, always in the same order)."""
     for _ in range(4):
         for x in range(env.Lx):
-            left_move(a, env, x, chi, cut_rel)
+            left_move(a, env, x, chi, cut_rel, log)
         a, env = rotate(a, env)
     return env
 
@@ -282,7 +309,7 @@ STALL_MAX = 1e-7       # ... counted as a stall only once the best delta is belo
 
 
 def ctmrg(a, env, chi, tol=1e-10, max_sweeps=200, min_sweeps=1, cut_rel=PROJ_CUT_REL,
-          stall_window=STALL_WINDOW, stall_max=STALL_MAX):
+          stall_window=STALL_WINDOW, stall_max=STALL_MAX, log=None):
     """Sweep until the corner spectra change by less than ``tol``; returns (env, sweeps, delta).
 
     The paper asks for a "sufficiently well-converged" environment (Appendix).  Reading: stop at
@@ -294,7 +321,7 @@ def ctmrg(a, env, chi, tol=1e-10, max_sweeps=200, min_sweeps=1, cut_rel=PROJ_CUT
     best, since = np.inf, 0
     n = 0
     for n in range(1, max_sweeps + 1):
-        env = sweep(a, env, chi, cut_rel)
+        env = sweep(a, env, chi, cut_rel, log)
         cur = corner_spectra(env, chi)
         delta = spectra_delta(cur, prev)
         prev = cur

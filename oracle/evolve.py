@@ -22,13 +22,18 @@ def ctm_state(GA, GB, lam):
 
 
 def converge_and_measure(GA, GB, lam, env, p, tol, max_sweeps):
+    """Converge the environment (warm from ``env``, or from the traced start when it is None) and
+    measure.  ``c8_margin`` in the result is the smallest ctmrg.cut_margin() over the 16 projector
+    computations of the last sweep: how far (in decades) the multiplet decisions at the chi cut
+    were from their thresholds when the readout was taken."""
     A, B, a = ctm_state(GA, GB, lam)
     if env is None:
         env = ctmrg.init_env(a, 2, 2, p['chi'], p['D'])
+    log = []
     env, sweeps, delta = ctmrg.ctmrg(a, env, p['chi'], tol=tol, max_sweeps=max_sweeps,
-                                     cut_rel=p.get('cut_rel', ctmrg.PROJ_CUT_REL))
+                                     cut_rel=p.get('cut_rel', ctmrg.PROJ_CUT_REL), log=log)
     obs = measure.observables(A, B, env, p['J'], p['V'], p['h'], p.get('d_A', 2))
-    obs.update(ctm_sweeps=sweeps, ctm_delta=delta)
+    obs.update(ctm_sweeps=sweeps, ctm_delta=delta, c8_margin=float(min(log[-16:])))
     return env, obs
 
 

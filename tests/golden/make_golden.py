@@ -21,16 +21,16 @@ from inputs import CONFIG1, CONFIG2  # noqa: E402
 from oracle import evolve  # noqa: E402
 
 KEYS = ("t", "nA", "nB", "imbalance", "tauzA", "tauzB", "energy", "purityA", "trunc_err_acc",
-        "ctm_sweeps", "ctm_delta")
+        "ctm_sweeps", "ctm_delta", "c8_margin")
 
 
 def _dump(path, params, out, seconds):
     rows = []
     for o in out:
-        r = {k: float(o[k]) for k in KEYS}
+        r = {k: min(float(o[k]), 99.0) for k in KEYS}
         r["lam"] = [[float(x) for x in row] for row in o["lam"]]
         # the same readout converged from the traced start (gauge independent, see evolve.run)
-        r["cold"] = {k: float(o["cold"][k]) for k in KEYS if k in o["cold"]}
+        r["cold"] = {k: min(float(o["cold"][k]), 99.0) for k in KEYS if k in o["cold"]}
         rows.append(r)
     with open(path, "w") as f:
         json.dump(dict(params=params, oracle_seconds=seconds, rows=rows), f, indent=1)

@@ -99,10 +99,12 @@ def _row_tol(sweeps):
 
 def _compare_rows(out, lam, g, keys, cold=False):
     """Observables per row.  Cold-start readouts depend only on the state and are held to _row_tol
-    of the oracle's cold sweeps at every time.  A warm-started readout is unique only where the
-    oracle's warm and cold readouts agree (at some times the truncated CTMRG has several fixed points
-    and the previous environment, whose gauge follows the simple update's singular-vector phases,
-    selects one); there it is held to _row_tol, elsewhere to 1e-3.  The simple-update state
+    of the oracle's cold sweeps.  A warm-started readout is unique only where the oracle's warm and
+    cold readouts agree (at some times the truncated CTMRG has several fixed points and the
+    previous environment, whose gauge follows the simple update's singular-vector phases, selects
+    one).  Rows whose multiplet decisions at the chi cut sat within two decades of the rule's
+    thresholds (c8_margin < 2) are not unique either.  Unique rows are held to _row_tol, the others
+    to 1e-3.  The simple-update state
     (discarded weight; bond spectra of the last row run) at 1e-10 relative / absolute."""
     errs = []
     for o, row in zip(out, g["rows"]):
@@ -110,6 +112,9 @@ def _compare_rows(out, lam, g, keys, cold=False):
         ref = row["cold"] if cold else row
         e = max(abs(o[k] - ref[k]) for k in keys)
         unique = cold or max(abs(row[k] - row["cold"][k]) for k in keys) < 1e-9
+        # C8: a multiplet decision at the chi cut within two decades of its threshold can go
+        # either way under rounding, and each way leads to a valid (different) readout
+        unique = unique and ref.get("c8_margin", 99.0) >= 2.0
         tol = _row_tol(ref["ctm_sweeps"]) if unique else 1e-3
         errs.append((row["t"], int(ref["ctm_sweeps"]), unique, e))
         assert e < tol, (row["t"], ref["ctm_sweeps"], unique, e)
