@@ -61,6 +61,7 @@ ipeps_status validate(const ipeps_params* p, std::string* why) {
   if (p->d_A != 2) { *why = "only d_A = 2 is implemented"; return IPEPS_EUNSUPPORTED; }
   if (p->D < 2 || p->D > 8) { *why = "D must be in [2, 8]"; return IPEPS_EINVAL; }
   if (p->chi < p->D * p->D) { *why = "chi must be >= D^2"; return IPEPS_EINVAL; }
+  if (p->chi > 2048) { *why = "chi above 2048 is not supported"; return IPEPS_EUNSUPPORTED; }
   if (p->trotter_order != 1 && p->trotter_order != 2) { *why = "trotter_order must be 1 or 2"; return IPEPS_EINVAL; }
   if (!(p->dt > 0.0)) { *why = "dt must be > 0"; return IPEPS_EINVAL; }
   if (p->precision != IPEPS_FP64 && p->precision != IPEPS_SPLIT_BF16X3) {
@@ -73,7 +74,10 @@ ipeps_status validate(const ipeps_params* p, std::string* why) {
   const bool sub = p->projector_svd == 2 ? k < N : (p->projector_svd == 1 ? false : N > 2 * k);
   if (p->projector_svd < 0 || p->projector_svd > 2) { *why = "projector_svd must be 0, 1 or 2"; return IPEPS_EINVAL; }
   if (sub && k > 256) { *why = "chi + 8 must not exceed 256 for the subspace projector SVD"; return IPEPS_EUNSUPPORTED; }
-  if (!jacobi_svd_fits(N, sub ? k : N)) { *why = "chi * D^2 too large for the projector SVD"; return IPEPS_EUNSUPPORTED; }
+  if (sub ? !jacobi_svd_supported(N, k) : !jacobi_svd_fits(N, N)) {
+    *why = "chi * D^2 too large for the projector SVD";
+    return IPEPS_EUNSUPPORTED;
+  }
   return IPEPS_OK;
 }
 
@@ -472,8 +476,19 @@ int ipeps_kernel_permute(const double* in, double* out, int rank, const int* dim
 int ipeps_kernel_svd(int m, int n, int batch, const double* A, double* U, double* S, double* V,
                      double tol, int max_sweeps, int* sweeps_out, void* stream) {
   if (m < n || n < 1 || batch < 1 || !A || !S) { set_thread_error("bad svd arguments"); return IPEPS_EINVAL; }
-  if (!jacobi_svd_fits(m, n)) { set_thread_error("svd size too large"); return IPEPS_EUNSUPPORTED; }
+  if (!jacobi_svd_supported(m, n)) { set_thread_error("svd size too large"); return IPEPS_EUNSUPPORTED; }
   cudaStream_t st = (cudaStream_t)stream;
+  // blocks too tall for shared memory keep their columns in a global-memory buffer
+  cplx* gwork = nullptr;
+  size_t gbytes = 0;
+  if (!jacobi_svd_fits(m, n)) {
+    gbytes = jacobi_svd_global_bytes(m, n, batch);
+    if (cudaMalloc(&gwork, gbytes) != cudaSuccess) {
+      cudaGetLastError();
+      set_thread_error("cudaMalloc failed");
+      return IPEPS_ENOMEM;
+    }
+  }
   std::vector<const void*> pa, pu, ps, pv;
   for (int b = 0; b < batch; ++b) {
     pa.push_back((const cplx*)A + (size_t)b * m * n);
@@ -485,6 +500,7 @@ int ipeps_kernel_svd(int m, int n, int batch, const double* A, double* U, double
   unsigned* derr = nullptr;
   if (cudaMalloc(&dp, sizeof(void*) * 4 * batch) != cudaSuccess || cudaMalloc(&derr, sizeof(unsigned)) != cudaSuccess) {
     cudaGetLastError();
+    cudaFree(gwork);
     set_thread_error("cudaMalloc failed");
     return IPEPS_ENOMEM;
   }
@@ -502,6 +518,7 @@ int ipeps_kernel_svd(int m, int n, int batch, const double* A, double* U, double
   d.S = (double* const*)(dp + 2 * batch);
   d.V = V ? (cplx* const*)(dp + 3 * batch) : nullptr; d.ldv = n;
   d.tol = tol; d.max_sweeps = max_sweeps; d.err = derr; d.sweeps_out = sweeps_out; d.skip = nullptr;
+  d.gwork = gwork; d.gwork_bytes = gbytes;
   int rc = jacobi_svd(d, st);
   unsigned e = 0;
   if (!rc) {
@@ -510,6 +527,7 @@ int ipeps_kernel_svd(int m, int n, int batch, const double* A, double* U, double
   }
   cudaFree(dp);
   cudaFree(derr);
+  cudaFree(gwork);
   if (rc) return rc;
   if (e & DEV_NONFINITE) { set_thread_error("non-finite input"); return IPEPS_ENAN; }
   if (e & DEV_JACOBI_CAP) { set_thread_error("sweep limit reached"); return IPEPS_ENOCONV; }

@@ -95,6 +95,12 @@ void ctm_carve(Ctx& c) {
   w.sub_done = a.take<int>((size_t)2 * B);
   w.sub_rounds = a.take<int>((size_t)2 * B);
   w.sub_res = a.take<double>((size_t)2 * B);
+  w.jgwork = nullptr;
+  w.jgwork_bytes = 0;
+  if (c.subspace && !jacobi_svd_fits(c.N, c.k)) {
+    w.jgwork_bytes = jacobi_svd_global_bytes(c.N, c.k, 2 * B);
+    w.jgwork = a.take<cplx>(w.jgwork_bytes / sizeof(cplx));
+  }
   if (c.precision == 1) {
     // largest split product of a left move: corner GEMM 3 / edge GEMM (chi^2 x D2^2 x D2^2, 8B),
     // halves (N^3, 4B), M (N^3, 2B), projectors (N chi N, 2B), edge absorption (chi D2chi N, 2B)
@@ -335,12 +341,40 @@ __global__ void proj_prep_kernel(const double* S, long long s_stride, int ns, co
   const cplx* Vq = V + (size_t)q * stride_uv;
   cplx* Uo = Us + (size_t)q * N * chi;
   cplx* Vo = Vs + (size_t)q * N * chi;
+  // Phase convention: the largest-magnitude entry of every kept u_j is made real and positive
+  // (u_j and v_j are multiplied by the same phase, so M = U S V^+ is unchanged).  It removes the
+  // arbitrary phases of the SVD from the new environment, so that consecutive sweeps produce
+  // nearly equal environment tensors once CTMRG settles and the warm-started subspace iteration
+  // of the next sweep starts close to its answer.
+  extern __shared__ double ph[];                 // [chi][2]: conj of the phase of column j
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (int j = warp; j < K; j += nwarps) {
+    double best = -1.0;
+    int bi = 0;
+    for (int i = lane; i < N; i += 32) {
+      const double v = cabs2(Uq[(size_t)i * ldu + j]);
+      if (v > best) { best = v; bi = i; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (lane == 0) {
+      const cplx u = Uq[(size_t)bi * ldu + j];
+      const double a = sqrt(cabs2(u));
+      ph[2 * j] = a > 0.0 ? u.x / a : 1.0;
+      ph[2 * j + 1] = a > 0.0 ? -u.y / a : 0.0;
+    }
+  }
+  __syncthreads();
   for (int idx = threadIdx.x; idx < N * chi; idx += blockDim.x) {
     const int i = idx / chi, j = idx % chi;
     if (j < K) {
       const double f = 1.0 / sqrt(s[j]);
-      Uo[idx] = cscale(Uq[(size_t)i * ldu + j], f);
-      Vo[idx] = cscale(Vq[(size_t)i * ldu + j], f);
+      const cplx e = cmk(ph[2 * j] * f, ph[2 * j + 1] * f);
+      Uo[idx] = cmul(Uq[(size_t)i * ldu + j], e);
+      Vo[idx] = cmul(Vq[(size_t)i * ldu + j], e);
     } else {
       Uo[idx] = cmk(0.0, 0.0);
       Vo[idx] = cmk(0.0, 0.0);
@@ -531,7 +565,8 @@ __global__ void sub_refill_kernel(cplx* Z, int N, int k, unsigned long long seed
 // M v_j = s_j u_j holds by construction), the triplets are converged when M^+ u_j = s_j v_j too:
 // residual_j = || (M^+ U_y)_j - s_j (V_f)_j || <= rtol * s_1 for the first min(k, chi + 1) columns.
 __global__ void sub_residual_kernel(const cplx* Z, const cplx* Vf, const double* S, int N, int k,
-                                    int ncheck, double rtol, int* done, int* rounds, double* prev) {
+                                    int ncheck, double rtol, double stag, int* done, int* rounds,
+                                    double* prev) {
   const int q = blockIdx.x;
   if (done[q]) return;
   const cplx* Zq = Z + (size_t)q * N * k;
@@ -556,9 +591,9 @@ __global__ void sub_residual_kernel(const cplx* Z, const cplx* Vf, const double*
   }
   if (threadIdx.x == 0) {
     const double r = sqrt(worst);
-    // accepted at rtol, or once the residual stops shrinking (factor 2 per round) below 1e-10 s_1:
+    // accepted at rtol, or once the residual stops shrinking (factor 2 per round) below stag s_1:
     // then it sits at the rounding floor of the small directions
-    if (r <= rtol * s[0] || (rounds[q] > 0 && r <= 1e-10 * s[0] && r > 0.5 * prev[q])) done[q] = 1;
+    if (r <= rtol * s[0] || (rounds[q] > 0 && r <= stag * s[0] && r > 0.5 * prev[q])) done[q] = 1;
     prev[q] = r;
     rounds[q] += 1;
   }
@@ -591,9 +626,11 @@ static int subspace_svd(Ctx& c, int f, int x, const cplx* R, const cplx* Rt) {
   yd.A = w.yA; yd.lda = k; yd.U = w.yU; yd.ldu = k; yd.S = w.yS; yd.V = w.yV; yd.ldv = k;
   yd.tol = 4e-16 * N; yd.max_sweeps = 60; yd.err = c.derr; yd.sweeps_out = nullptr;
   yd.skip = w.sub_done;
+  yd.gwork = w.jgwork; yd.gwork_bytes = w.jgwork_bytes;
   SvdDesc zd = yd;
   zd.A = w.zA; zd.U = w.zU; zd.S = w.zS; zd.V = nullptr;
   const int ncheck = chi + 1 < k ? chi + 1 : k;
+  const double rtol = 1e-12, stag = 1e-10;
   for (int it = 0; it < rounds; ++it) {
     GemmDesc g = gd(N, k, N, 2 * B);            // Y = M V
     g.A = w.M; g.sA = N2; g.lda = N; g.B = w.Vw; g.sB = Nk; g.ldb = k;
@@ -609,8 +646,8 @@ static int subspace_svd(Ctx& c, int f, int x, const cplx* R, const cplx* Rt) {
     g.B = w.Uy; g.sB = Nk; g.ldb = k; g.C = w.Zsub; g.sC = Nk; g.ldc = k; g.skip = w.sub_done;
     if ((rc = zgemm_f64(g, st))) return rc;
     IPEPS_LAUNCH(K_PROJ_PREP, 0, st,
-                 sub_residual_kernel<<<2 * B, 256, 0, st>>>(w.Zsub, slot, w.Sy, N, k, ncheck, 1e-12,
-                                                            w.sub_done, w.sub_rounds, w.sub_res));
+                 sub_residual_kernel<<<2 * B, 256, 0, st>>>(w.Zsub, slot, w.Sy, N, k, ncheck, rtol,
+                                                            stag, w.sub_done, w.sub_rounds, w.sub_res));
     if (it + 1 == rounds) break;
     IPEPS_LAUNCH(K_PROJ_PREP, 0, st,
                  sub_refill_kernel<<<2 * B, 256, 0, st>>>(w.Zsub, N, k, c.seed, stream_id * 1000 + it,
@@ -622,7 +659,7 @@ static int subspace_svd(Ctx& c, int f, int x, const cplx* R, const cplx* Rt) {
   }
   c.slot_warm[f][x] = true;
   IPEPS_LAUNCH(K_PROJ_PREP, 0, st,
-               proj_prep_kernel<<<2 * B, 256, 0, st>>>(w.Sy, k, k, w.Uy, slot, N, chi, k, Nk, w.Us,
+               proj_prep_kernel<<<2 * B, 256, 2 * chi * sizeof(double), st>>>(w.Sy, k, k, w.Uy, slot, N, chi, k, Nk, w.Us,
                                                        w.Vs, w.kept, kDegenRtol, kDegenAbs, kTinyRel, c.cut_rel));
   return 0;
 }
@@ -672,7 +709,7 @@ static int left_move(Ctx& c, int f, int x) {
     sd.tol = 4e-16 * N; sd.max_sweeps = 80; sd.err = c.derr; sd.sweeps_out = nullptr; sd.skip = nullptr;
     if ((rc = jacobi_svd(sd, st))) return rc;
     IPEPS_LAUNCH(K_PROJ_PREP, 0, st,
-                 proj_prep_kernel<<<2 * B, 256, 0, st>>>(w.S, N, N, w.U, w.V, N, chi, N, N2, w.Us,
+                 proj_prep_kernel<<<2 * B, 256, 2 * chi * sizeof(double), st>>>(w.S, N, N, w.U, w.V, N, chi, N, N2, w.Us,
                                                          w.Vs, w.kept, kDegenRtol, kDegenAbs, kTinyRel, c.cut_rel));
   } else {
     if ((rc = subspace_svd(c, f, x, R, Rt))) return rc;

@@ -67,6 +67,8 @@ struct CtmWork {
   int* sub_done;                     // [2B] converged flags of the subspace iteration
   int* sub_rounds;                   // [2B] rounds used (diagnostics)
   double* sub_res;                   // [2B] previous residual (stagnation test)
+  cplx* jgwork;                      // Jacobi column storage when N x k blocks exceed SMEM (or null)
+  size_t jgwork_bytes;
   const cplx* const* yA; cplx* const* yU; double* const* yS; cplx* const* yV;   // Jacobi of Y
   const cplx* const* zA; cplx* const* zU; double* const* zS;                    // Jacobi of Z
 };

@@ -203,9 +203,12 @@ jacobi_kernel(JacobiArgs args) {
   if (d.skip && d.skip[prob]) return;
 
   extern __shared__ __align__(16) unsigned char jsm_raw[];
-  cplx* colA = reinterpret_cast<cplx*>(jsm_raw);           // colA[j * ra + i]
+  // the CTA's row slices of the columns: in shared memory, or in its own region of d.gwork
+  cplx* colA = d.gwork ? d.gwork + (size_t)blockIdx.x * np * (ra + rw)
+                       : reinterpret_cast<cplx*>(jsm_raw);   // colA[j * ra + i]
   cplx* colW = colA + (size_t)np * ra;                      // colW[j * rw + i]
-  double* part = reinterpret_cast<double*>(colW + (size_t)np * rw);   // [2][JCS][npairs][4]
+  double* part = d.gwork ? reinterpret_cast<double*>(jsm_raw)
+                         : reinterpret_cast<double*>(colW + (size_t)np * rw);   // [2][JCS][npairs][4]
   double* rot = part + 2 * JCS * npairs * 4;                // [npairs][4]: c, s, er, ei
   int* flags = reinterpret_cast<int*>(rot + npairs * 4);    // [npairs] + any + nonfinite
 
@@ -406,14 +409,37 @@ bool jacobi_svd_fits(int m, int n) {
   return m >= n && n >= 1 && jacobi_svd_smem_bytes(m, n) <= 200 * 1024;
 }
 
+// shared memory left when the columns live in global memory: partial sums, rotations, flags
+static size_t jacobi_small_smem_bytes(int m, int n) {
+  int np, ra, rw;
+  jacobi_layout(m, n, &np, &ra, &rw);
+  const size_t npairs = np / 2;
+  return (2 * JCS * npairs * 4 + npairs * 4) * sizeof(double) + (npairs + 2 + np) * sizeof(int) + 64;
+}
+
+bool jacobi_svd_supported(int m, int n) {
+  return m >= n && n >= 1 && jacobi_small_smem_bytes(m, n) <= 200 * 1024;
+}
+
+size_t jacobi_svd_global_bytes(int m, int n, int batch) {
+  int np, ra, rw;
+  jacobi_layout(m, n, &np, &ra, &rw);
+  return (size_t)batch * JCS * np * (ra + rw) * sizeof(cplx);
+}
+
 int jacobi_svd(const SvdDesc& d, cudaStream_t st) {
   if (d.batch <= 0) return 0;
-  if (!jacobi_svd_fits(d.m, d.n))
-    return cuda_fail(cudaErrorInvalidValue, "jacobi_svd size", __FILE__, __LINE__);
   JacobiArgs a;
   a.d = d;
+  const bool in_smem = jacobi_svd_fits(d.m, d.n);
+  if (in_smem) {
+    a.d.gwork = nullptr;
+  } else if (!jacobi_svd_supported(d.m, d.n) || !d.gwork ||
+             d.gwork_bytes < jacobi_svd_global_bytes(d.m, d.n, d.batch)) {
+    return cuda_fail(cudaErrorInvalidValue, "jacobi_svd size", __FILE__, __LINE__);
+  }
   jacobi_layout(d.m, d.n, &a.np, &a.ra, &a.rw);
-  size_t smem = jacobi_svd_smem_bytes(d.m, d.n);
+  size_t smem = in_smem ? jacobi_svd_smem_bytes(d.m, d.n) : jacobi_small_smem_bytes(d.m, d.n);
   static bool attr_set = false;
   if (!attr_set) {
     IPEPS_CUDA_TRY(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

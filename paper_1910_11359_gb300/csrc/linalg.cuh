@@ -44,10 +44,18 @@ struct SvdDesc {
   unsigned* err;       // device error word (DevErr bits)
   int* sweeps_out;     // optional: sweeps used per problem (1 = the input columns were orthogonal)
   const int* skip;     // optional [batch]: problems with skip[b] != 0 are left untouched
+  // optional global-memory column storage for blocks whose rows do not fit in shared memory
+  // (jacobi_svd_global_bytes(m, n, batch) bytes; the columns then live in L2 instead of SMEM)
+  cplx* gwork = nullptr;
+  size_t gwork_bytes = 0;
 };
 
 int jacobi_svd(const SvdDesc& d, cudaStream_t st);
 size_t jacobi_svd_smem_bytes(int m, int n);
+// the columns of [A; W] fit in the shared memory of the 8-CTA cluster
 bool jacobi_svd_fits(int m, int n);
+// the block can be factorised at all (with gwork when it does not fit in shared memory)
+bool jacobi_svd_supported(int m, int n);
+size_t jacobi_svd_global_bytes(int m, int n, int batch);
 
 }  // namespace ipeps

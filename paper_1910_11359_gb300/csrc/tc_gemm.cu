@@ -246,76 +246,100 @@ __device__ __forceinline__ void split_bf16(double x, __nv_bfloat16* hi, __nv_bfl
   *lo = __float2bfloat16_rn((float)(x - (double)__bfloat162float(h)));
 }
 
-// element (row, col) of op(P) for a complex operand stored with leading dimension ld
-__device__ __forceinline__ cplx op_elem(const cplx* P, long long ld, int op, int row, int col) {
-  if (op == OP_N) return P[(long long)row * ld + col];
-  const cplx v = P[(long long)col * ld + row];
-  return op == OP_C ? cconj(v) : v;
-}
+// The operands are prepared tile by tile: a 32 x 32 tile of op(A) (rows x K) or of op(B)^T
+// (columns x K) is read with coalesced loads along whichever index is contiguous in memory, held
+// in shared memory, and written out along K, where each complex element becomes its 12 (A) or 6 (B)
+// BF16 entries.  Grid: (K tiles, row tiles, batch), so no integer division per element.  Columns
+// c >= 6K of both operands are zeroed by the host; rows beyond 2M (A3) or N (B3) only feed output
+// entries that are never read.
+constexpr int PT = 32;
 
-// A3[b][i][c], i < Mp (2M real rows, zero beyond), c < Kp (6K used):
-//   segment c / 2K: 0, 1 -> hi part, 2 -> lo part of A_big[i][c % 2K]
-__global__ void prep_a_kernel(GemmDesc g, __nv_bfloat16* A3, int Mp, int Kp) {
-  const int M = g.M, K = g.K;
-  const long long per = (long long)Mp * Kp;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < per * g.batch;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int b = (int)(idx / per);
-    const int i = (int)((idx % per) / Kp), c = (int)(idx % Kp);
-    __nv_bfloat16 out = __float2bfloat16_rn(0.f);
-    if (i < 2 * M && c < 6 * K) {
-      const int seg = c / (2 * K), cc = c % (2 * K);
-      const cplx* A = g.Aptr ? g.Aptr[b] : g.A + (long long)b * g.sA;
-      const int r = i < M ? i : i - M;
-      const cplx v = op_elem(A, g.lda, g.opA, r, cc < K ? cc : cc - K);
-      double x;
-      if (i < M) x = cc < K ? v.x : -v.y;      // [Ar, -Ai]
-      else x = cc < K ? v.y : v.x;             // [Ai,  Ar]
-      __nv_bfloat16 hi, lo;
-      split_bf16(x, &hi, &lo);
-      out = seg == 2 ? lo : hi;
+// tile[r][k] = element (row0 + r, k0 + k) of the operand seen as rows x K, stored either
+// K-contiguous (P[row * ld + k]) or row-contiguous (P[k * ld + row]); conjugated for OP_C
+__device__ __forceinline__ void load_tile(cplx (*tile)[PT + 1], const cplx* P, long long ld, bool kcontig,
+                                          bool cj, int row0, int k0, int rows, int K) {
+  const int tx = threadIdx.x;
+  for (int a = threadIdx.y; a < PT; a += blockDim.y) {
+    if (kcontig) {
+      const int r = row0 + a, k = k0 + tx;
+      const cplx v = (r < rows && k < K) ? P[(long long)r * ld + k] : cmk(0.0, 0.0);
+      tile[a][tx] = cj ? cconj(v) : v;
+    } else {
+      const int k = k0 + a, r = row0 + tx;
+      const cplx v = (r < rows && k < K) ? P[(long long)k * ld + r] : cmk(0.0, 0.0);
+      tile[tx][a] = cj ? cconj(v) : v;
     }
-    A3[idx] = out;
   }
 }
 
-// B3t[b][j][c], j < Np (N used), c < Kp: segment 0, 2 -> hi, 1 -> lo of B_big[c % 2K][j]
-__global__ void prep_b_kernel(GemmDesc g, __nv_bfloat16* B3t, int Np, int Kp) {
-  const int N = g.N, K = g.K;
-  const long long per = (long long)Np * Kp;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < per * g.batch;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int b = (int)(idx / per);
-    const int j = (int)((idx % per) / Kp), c = (int)(idx % Kp);
-    __nv_bfloat16 out = __float2bfloat16_rn(0.f);
-    if (j < N && c < 6 * K) {
-      const int seg = c / (2 * K), cc = c % (2 * K);
-      const cplx* B = g.Bptr ? g.Bptr[b] : g.B + (long long)b * g.sB;
-      const cplx v = op_elem(B, g.ldb, g.opB, cc < K ? cc : cc - K, j);
-      const double x = cc < K ? v.x : v.y;     // [Br; Bi]
-      __nv_bfloat16 hi, lo;
-      split_bf16(x, &hi, &lo);
-      out = seg == 1 ? lo : hi;
-    }
-    B3t[idx] = out;
+// A3[b] (Mp x Kp): row r < M holds [Ar | -Ai], row M + r holds [Ai | Ar]; each 2K-wide segment
+// appears as hi, hi, lo.
+__global__ void __launch_bounds__(256) prep_a_kernel(GemmDesc g, __nv_bfloat16* A3, int Mp, int Kp) {
+  __shared__ cplx tile[PT][PT + 1];
+  const int b = blockIdx.z, M = g.M, K = g.K;
+  const int row0 = blockIdx.y * PT, k0 = blockIdx.x * PT;
+  const cplx* A = g.Aptr ? g.Aptr[b] : g.A + (long long)b * g.sA;
+  // op(A)[r][k]: OP_N reads A[r * lda + k]; OP_T and OP_C read A[k * lda + r]
+  load_tile(tile, A, g.lda, g.opA == OP_N, g.opA == OP_C, row0, k0, M, K);
+  __syncthreads();
+  const int k = k0 + threadIdx.x;
+  if (k >= K) return;
+  for (int a = threadIdx.y; a < PT; a += blockDim.y) {
+    const int r = row0 + a;
+    if (r >= M) break;
+    const cplx v = tile[a][threadIdx.x];
+    __nv_bfloat16 rh, rl, ih, il, mh, ml;
+    split_bf16(v.x, &rh, &rl);
+    split_bf16(v.y, &ih, &il);
+    split_bf16(-v.y, &mh, &ml);
+    __nv_bfloat16* up = A3 + ((long long)b * Mp + r) * Kp;        // row r
+    __nv_bfloat16* dn = A3 + ((long long)b * Mp + M + r) * Kp;    // row M + r
+    up[k] = rh;          up[K + k] = mh;
+    up[2 * K + k] = rh;  up[3 * K + k] = mh;
+    up[4 * K + k] = rl;  up[5 * K + k] = ml;
+    dn[k] = ih;          dn[K + k] = rh;
+    dn[2 * K + k] = ih;  dn[3 * K + k] = rh;
+    dn[4 * K + k] = il;  dn[5 * K + k] = rl;
   }
 }
 
-// C[b][i][j] = alpha (C32[i][j] + i C32[M + i][j]) + beta C[b][i][j]
-__global__ void gather_c_kernel(GemmDesc g, const float* C32, int Mp, int Np) {
-  const int M = g.M, N = g.N;
-  const long long per = (long long)M * N;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < per * g.batch;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int b = (int)(idx / per);
-    const int i = (int)((idx % per) / N), j = (int)(idx % N);
-    const float* cb = C32 + (long long)b * Mp * Np;
-    cplx v = cmk((double)cb[(long long)i * Np + j], (double)cb[(long long)(M + i) * Np + j]);
-    cplx* Cb = g.Cptr ? g.Cptr[b] : g.C + (long long)b * g.sC;
-    const long long o = (long long)i * g.ldc + j;
-    cplx r = cmul(g.alpha, v);
-    if (g.beta.x != 0.0 || g.beta.y != 0.0) r = cadd(r, cmul(g.beta, Cb[o]));
-    Cb[o] = r;
+// B3t[b] (Np x Kp), row j = column j of B3 = [B_hi; B_lo; B_hi] with B_big = [Br; Bi] (2K x N)
+__global__ void __launch_bounds__(256) prep_b_kernel(GemmDesc g, __nv_bfloat16* B3t, int Np, int Kp) {
+  __shared__ cplx tile[PT][PT + 1];
+  const int b = blockIdx.z, N = g.N, K = g.K;
+  const int row0 = blockIdx.y * PT, k0 = blockIdx.x * PT;
+  const cplx* B = g.Bptr ? g.Bptr[b] : g.B + (long long)b * g.sB;
+  // op(B)^T[j][k] = op(B)[k][j]: OP_N reads B[k * ldb + j]; OP_T and OP_C read B[j * ldb + k]
+  load_tile(tile, B, g.ldb, g.opB != OP_N, g.opB == OP_C, row0, k0, N, K);
+  __syncthreads();
+  const int k = k0 + threadIdx.x;
+  if (k >= K) return;
+  for (int a = threadIdx.y; a < PT; a += blockDim.y) {
+    const int j = row0 + a;
+    if (j >= N) break;
+    const cplx v = tile[a][threadIdx.x];
+    __nv_bfloat16 rh, rl, ih, il;
+    split_bf16(v.x, &rh, &rl);
+    split_bf16(v.y, &ih, &il);
+    __nv_bfloat16* row = B3t + ((long long)b * Np + j) * Kp;
+    row[k] = rh;          row[K + k] = ih;
+    row[2 * K + k] = rl;  row[3 * K + k] = il;
+    row[4 * K + k] = rh;  row[5 * K + k] = ih;
+  }
+}
+
+// C[b][i][j] = alpha (C32[i][j] + i C32[M + i][j]) + beta C[b][i][j]; grid (column chunks, rows, batch)
+__global__ void __launch_bounds__(256) gather_c_kernel(GemmDesc g, const float* C32, int Mp, int Np) {
+  const int b = blockIdx.z, i = blockIdx.y;
+  const float* top = C32 + ((long long)b * Mp + i) * Np;
+  const float* bot = C32 + ((long long)b * Mp + g.M + i) * Np;
+  cplx* Cb = g.Cptr ? g.Cptr[b] : g.C + (long long)b * g.sC;
+  cplx* crow = Cb + (long long)i * g.ldc;
+  const bool use_beta = g.beta.x != 0.0 || g.beta.y != 0.0;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < g.N; j += gridDim.x * blockDim.x) {
+    cplx r = cmul(g.alpha, cmk((double)top[j], (double)bot[j]));
+    if (use_beta) r = cadd(r, cmul(g.beta, crow[j]));
+    crow[j] = r;
   }
 }
 
@@ -411,12 +435,22 @@ int zgemm_split_bf16(const GemmDesc& g, void* work, size_t work_bytes, unsigned*
   __nv_bfloat16* B3 = (__nv_bfloat16*)w;
   w += ((size_t)Np * Kp * 2 * g.batch + 1023) & ~(size_t)1023;
   float* C32 = (float*)w;
-  const int blocks = 152 * 8;
-  IPEPS_LAUNCH(K_TC_PREP, 0, st, prep_a_kernel<<<blocks, 256, 0, st>>>(g, A3, Mp, Kp));
-  IPEPS_LAUNCH(K_TC_PREP, 0, st, prep_b_kernel<<<blocks, 256, 0, st>>>(g, B3, Np, Kp));
+  if (g.batch > 65535 || g.M > 65535) return cuda_fail(cudaErrorInvalidValue, "split gemm grid", __FILE__, __LINE__);
+  // zero K padding (columns 6K .. Kp) of both operands; the GEMM reads it
+  if (Kp > 6 * g.K) {
+    const size_t pitch = (size_t)Kp * 2, width = (size_t)(Kp - 6 * g.K) * 2;
+    IPEPS_CUDA_TRY(cudaMemset2DAsync(A3 + 6 * g.K, pitch, 0, width, (size_t)Mp * g.batch, st));
+    IPEPS_CUDA_TRY(cudaMemset2DAsync(B3 + 6 * g.K, pitch, 0, width, (size_t)Np * g.batch, st));
+  }
+  const dim3 pblk(PT, 8);
+  const dim3 pa((g.K + PT - 1) / PT, (g.M + PT - 1) / PT, g.batch);
+  const dim3 pb((g.K + PT - 1) / PT, (g.N + PT - 1) / PT, g.batch);
+  IPEPS_LAUNCH(K_TC_PREP, 0, st, prep_a_kernel<<<pa, pblk, 0, st>>>(g, A3, Mp, Kp));
+  IPEPS_LAUNCH(K_TC_PREP, 0, st, prep_b_kernel<<<pb, pblk, 0, st>>>(g, B3, Np, Kp));
   IPEPS_CUDA_TRY(cudaGetLastError());
   if (int rc = gemm_bf16_raw(A3, B3, C32, Mp, Np, Kp, g.batch, bn, err, st)) return rc;
-  IPEPS_LAUNCH(K_TC_PREP, 0, st, gather_c_kernel<<<blocks, 256, 0, st>>>(g, C32, Mp, Np));
+  const dim3 gc((g.N + 255) / 256, g.M, g.batch);
+  IPEPS_LAUNCH(K_TC_PREP, 0, st, gather_c_kernel<<<gc, 256, 0, st>>>(g, C32, Mp, Np));
   IPEPS_CUDA_TRY(cudaGetLastError());
   return 0;
 }

@@ -92,3 +92,24 @@ def test_gate_matches_oracle(J, V, h, delta):
     rc = _lib().ipeps_kernel_gate(J, V, h, delta, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
     assert rc == 0
     assert np.max(np.abs(out - model.gate(J, V, h, delta))) < 1e-14
+
+
+@pytest.mark.parametrize("m,n", [(2400, 40), (1300, 100)])
+def test_jacobi_svd_columns_in_global_memory(m, n):
+    """Blocks whose row slices exceed shared memory keep their columns in a global buffer."""
+    batch = 2
+    A = _rand((batch, m, n), 11)
+    A[1] = A[1] @ np.diag(np.logspace(0, -10, n))       # graded spectrum
+    dA = _dev(A)
+    dU = torch.zeros((batch, m, n), dtype=torch.complex128, device="cuda")
+    dS = torch.zeros((batch, n), dtype=torch.float64, device="cuda")
+    dV = torch.zeros((batch, n, n), dtype=torch.complex128, device="cuda")
+    rc = _lib().ipeps_kernel_svd(m, n, batch, _p(dA), _p(dU), _p(dS), _p(dV), 4e-16 * m, 80, None, None)
+    assert rc == 0
+    U, S, V = dU.cpu().numpy(), dS.cpu().numpy(), dV.cpu().numpy()
+    for b in range(batch):
+        s_ref = np.linalg.svd(A[b], compute_uv=False)
+        assert np.max(np.abs(S[b] - s_ref)) < 1e-12 * s_ref[0]
+        rec = (U[b] * S[b]) @ V[b].conj().T
+        assert np.max(np.abs(rec - A[b])) < 1e-12 * s_ref[0]
+        assert np.max(np.abs(V[b].conj().T @ V[b] - np.eye(n))) < 1e-13
