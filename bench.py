@@ -159,6 +159,23 @@ def reference_main(args):
     return 0
 
 
+# ----------------------------------------------------------------------------- replicas
+def reduce_max_ms(total_ms, dist, device):
+    """Max over ranks of a replica's timed region (every rank receives it); no data-path collective
+    exists: each rank runs its own independent instances."""
+    if dist is None:
+        return total_ms
+    import torch
+    t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank, world, max_ms):
+    """Whole-job throughput of `world` replicas: all units processed over the slowest rank's time."""
+    return units_per_rank * world / (max_ms * 1e-3)
+
+
 # ----------------------------------------------------------------------------- native arm
 def native_main(args):
     import torch
@@ -213,14 +230,11 @@ def native_main(args):
         prof = pkg.profile_read()
         pkg.profile_enable(False)
         launches = pkg.launch_count() - launches0
+        total_ms = reduce_max_ms(total_ms, dist, "cuda")
         if dist is not None:
-            t = torch.tensor([total_ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_ms = float(t.item())
             dist.barrier()
         clk = clocks.stop()
-        steps_done = B * STEPS_PER_READOUT * args.steps * world
-        value = steps_done / (total_ms * 1e-3)
+        value = replica_throughput(B * STEPS_PER_READOUT * args.steps, world, total_ms)
 
         # end to end through the public API with host buffers (pinned), copies inside the timing
         GA, GB = sim.get_tensors()
