@@ -118,7 +118,8 @@ int permute_c128(const cplx* in, cplx* out, int rank, const int* dims, const int
 }
 
 // ------------------------------------------------------------------------------------ Jacobi SVD
-constexpr int JCS = 8;          // CTAs per cluster (portable cluster size)
+constexpr int JCS = 8;          // CTAs per cluster for most blocks (portable cluster size)
+constexpr int JCS_TALL = 16;    // tall blocks (m >= 1024) on 16-CTA clusters where the part allows
 // Columns whose squared norm is below JTINY take part in no rotation: their squared entries sit in
 // or near the subnormal range, where the rotation's phase cannot be formed accurately.
 constexpr double JTINY = 1e-250;
@@ -189,12 +190,12 @@ __device__ __forceinline__ int jacobi_rotation(double al, double be, double gr, 
   return 1;
 }
 
-__global__ void __cluster_dims__(JCS, 1, 1) __launch_bounds__(JTHREADS)
-jacobi_kernel(JacobiArgs args) {
+template <int CS>
+__global__ void __launch_bounds__(JTHREADS) jacobi_kernel(JacobiArgs args) {
   cg::cluster_group cluster = cg::this_cluster();
   const SvdDesc& d = args.d;
   const int rank = (int)cluster.block_rank();
-  const int prob = blockIdx.x / JCS;
+  const int prob = blockIdx.x / CS;
   const int np = args.np, ra = args.ra, rw = args.rw;
   const int npairs = np / 2;
   const int m = d.m, n = d.n;
@@ -208,8 +209,8 @@ jacobi_kernel(JacobiArgs args) {
                        : reinterpret_cast<cplx*>(jsm_raw);   // colA[j * ra + i]
   cplx* colW = colA + (size_t)np * ra;                      // colW[j * rw + i]
   double* part = d.gwork ? reinterpret_cast<double*>(jsm_raw)
-                         : reinterpret_cast<double*>(colW + (size_t)np * rw);   // [2][JCS][npairs][4]
-  double* rot = part + 2 * JCS * npairs * 4;                // [npairs][4]: c, s, er, ei
+                         : reinterpret_cast<double*>(colW + (size_t)np * rw);   // [2][CS][npairs][4]
+  double* rot = part + 2 * CS * npairs * 4;                // [npairs][4]: c, s, er, ei
   int* flags = reinterpret_cast<int*>(rot + npairs * 4);    // [npairs] + any + nonfinite
 
   const cplx* A = d.A[prob];
@@ -237,7 +238,7 @@ jacobi_kernel(JacobiArgs args) {
     for (int r = 0; r < nrounds; ++r, ++gcount) {
       const int buf = (int)(gcount & 1);
       // slot of this CTA's partial sums inside every CTA's buffer
-      const size_t myslot = ((size_t)buf * JCS + rank) * npairs * 4;
+      const size_t myslot = ((size_t)buf * CS + rank) * npairs * 4;
       // dot products: ppw pairs per warp, lpp lanes per pair, reduced by shuffles within the group
       for (int pb = warp * ppw; pb < npairs; pb += nwarps * ppw) {
         const int p = pb + slot;
@@ -262,7 +263,7 @@ jacobi_kernel(JacobiArgs args) {
         // push the partials into every CTA of the cluster (remote stores do not stall; the
         // cluster barrier below makes them visible), so the reduction reads only local memory
         if (valid)
-          for (int q = sub; q < JCS; q += lpp) {
+          for (int q = sub; q < CS; q += lpp) {
             double* dst = cluster.map_shared_rank(part, q) + myslot + p * 4;
             dst[0] = al; dst[1] = be; dst[2] = gr; dst[3] = gi;
           }
@@ -275,7 +276,7 @@ jacobi_kernel(JacobiArgs args) {
         const int p = pb + (lane >> 2), comp = lane & 3;
         double acc = 0.0;
         if (p < npairs)
-          for (int q = 0; q < JCS; ++q) acc += part[((size_t)buf * JCS + q) * npairs * 4 + p * 4 + comp];
+          for (int q = 0; q < CS; ++q) acc += part[((size_t)buf * CS + q) * npairs * 4 + p * 4 + comp];
         const int base = lane & ~3;
         const double al = __shfl_sync(0xffffffffu, acc, base);
         const double be = __shfl_sync(0xffffffffu, acc, base + 1);
@@ -347,7 +348,7 @@ jacobi_kernel(JacobiArgs args) {
   __syncthreads();
   for (int j = tid; j < np; j += JTHREADS) {
     double s = 0.0;
-    for (int q = 0; q < JCS; ++q) s += cluster.map_shared_rank(norms, q)[j];
+    for (int q = 0; q < CS; ++q) s += cluster.map_shared_rank(norms, q)[j];
     sig[j] = sqrt(s);
   }
   __syncthreads();
@@ -391,68 +392,125 @@ jacobi_kernel(JacobiArgs args) {
   cluster.sync();   // no CTA leaves while its shared memory may still be read by the others
 }
 
-static void jacobi_layout(int m, int n, int* np, int* ra, int* rw) {
+static void jacobi_layout(int m, int n, int cs, int* np, int* ra, int* rw) {
   *np = n + (n & 1);
-  *ra = (m + JCS - 1) / JCS;
-  *rw = (n + JCS - 1) / JCS;
+  *ra = (m + cs - 1) / cs;
+  *rw = (n + cs - 1) / cs;
 }
 
-size_t jacobi_svd_smem_bytes(int m, int n) {
+static size_t smem_bytes_cs(int m, int n, int cs) {
   int np, ra, rw;
-  jacobi_layout(m, n, &np, &ra, &rw);
+  jacobi_layout(m, n, cs, &np, &ra, &rw);
   size_t npairs = np / 2;
-  return (size_t)np * (ra + rw) * sizeof(cplx) + (2 * JCS * npairs * 4 + npairs * 4) * sizeof(double) +
+  return (size_t)np * (ra + rw) * sizeof(cplx) + (2 * (size_t)cs * npairs * 4 + npairs * 4) * sizeof(double) +
          (npairs + 2 + np) * sizeof(int) + 64;
 }
 
-bool jacobi_svd_fits(int m, int n) {
-  return m >= n && n >= 1 && jacobi_svd_smem_bytes(m, n) <= 200 * 1024;
+// shared memory left when the columns live in global memory: partial sums, rotations, flags
+static size_t small_smem_bytes_cs(int m, int n, int cs) {
+  int np, ra, rw;
+  jacobi_layout(m, n, cs, &np, &ra, &rw);
+  const size_t npairs = np / 2;
+  return (2 * (size_t)cs * npairs * 4 + npairs * 4) * sizeof(double) + (npairs + 2 + np) * sizeof(int) + 64;
 }
 
-// shared memory left when the columns live in global memory: partial sums, rotations, flags
-static size_t jacobi_small_smem_bytes(int m, int n) {
+static size_t global_bytes_cs(int m, int n, int batch, int cs) {
   int np, ra, rw;
-  jacobi_layout(m, n, &np, &ra, &rw);
-  const size_t npairs = np / 2;
-  return (2 * JCS * npairs * 4 + npairs * 4) * sizeof(double) + (npairs + 2 + np) * sizeof(int) + 64;
+  jacobi_layout(m, n, cs, &np, &ra, &rw);
+  return (size_t)batch * cs * np * (ra + rw) * sizeof(cplx);
+}
+
+// The public size predicates assume 8-CTA clusters (the conservative choice); a launch on 16-CTA
+// clusters needs no more shared memory per CTA and at most jacobi_svd_global_bytes of columns.
+size_t jacobi_svd_smem_bytes(int m, int n) { return smem_bytes_cs(m, n, JCS); }
+
+bool jacobi_svd_fits(int m, int n) {
+  return m >= n && n >= 1 && smem_bytes_cs(m, n, JCS) <= 200 * 1024;
 }
 
 bool jacobi_svd_supported(int m, int n) {
-  return m >= n && n >= 1 && jacobi_small_smem_bytes(m, n) <= 200 * 1024;
+  return m >= n && n >= 1 && small_smem_bytes_cs(m, n, JCS) <= 200 * 1024;
 }
 
 size_t jacobi_svd_global_bytes(int m, int n, int batch) {
-  int np, ra, rw;
-  jacobi_layout(m, n, &np, &ra, &rw);
-  return (size_t)batch * JCS * np * (ra + rw) * sizeof(cplx);
+  return std::max(global_bytes_cs(m, n, batch, JCS), global_bytes_cs(m, n, batch, JCS_TALL));
+}
+
+// 16-CTA clusters are a non-portable size: used when the device accepts them for this kernel
+static bool tall_clusters_available() {
+  static int state = -1;
+  if (state < 0) {
+    state = 0;
+    if (cudaFuncSetAttribute(jacobi_kernel<JCS_TALL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+            cudaSuccess &&
+        cudaFuncSetAttribute(jacobi_kernel<JCS_TALL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024 + 1024) == cudaSuccess) {
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = JCS_TALL;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.gridDim = dim3(JCS_TALL);
+      cfg.blockDim = dim3(JTHREADS);
+      cfg.dynamicSmemBytes = 200 * 1024;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      int nclusters = 0;
+      if (cudaOccupancyMaxActiveClusters(&nclusters, jacobi_kernel<JCS_TALL>, &cfg) == cudaSuccess &&
+          nclusters > 0)
+        state = 1;
+    }
+    cudaGetLastError();
+  }
+  return state == 1;
+}
+
+template <int CS>
+static int launch_jacobi(const JacobiArgs& a, size_t smem, int batch, cudaStream_t st) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    IPEPS_CUDA_TRY(cudaFuncSetAttribute(jacobi_kernel<CS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        200 * 1024 + 1024));
+    attr_set = true;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(batch * CS);
+  cfg.blockDim = dim3(JTHREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  IPEPS_LAUNCH(K_JACOBI, 0, st, IPEPS_CUDA_TRY(cudaLaunchKernelEx(&cfg, jacobi_kernel<CS>, a)));
+  return 0;
 }
 
 int jacobi_svd(const SvdDesc& d, cudaStream_t st) {
   if (d.batch <= 0) return 0;
+  if (!jacobi_svd_supported(d.m, d.n))
+    return cuda_fail(cudaErrorInvalidValue, "jacobi_svd size", __FILE__, __LINE__);
+  const int cs = (d.m >= 1024 && tall_clusters_available()) ? JCS_TALL : JCS;
   JacobiArgs a;
   a.d = d;
-  const bool in_smem = jacobi_svd_fits(d.m, d.n);
+  const bool in_smem = smem_bytes_cs(d.m, d.n, cs) <= 200 * 1024;
   if (in_smem) {
     a.d.gwork = nullptr;
-  } else if (!jacobi_svd_supported(d.m, d.n) || !d.gwork ||
-             d.gwork_bytes < jacobi_svd_global_bytes(d.m, d.n, d.batch)) {
+  } else if (!d.gwork || d.gwork_bytes < global_bytes_cs(d.m, d.n, d.batch, cs)) {
     return cuda_fail(cudaErrorInvalidValue, "jacobi_svd size", __FILE__, __LINE__);
   }
-  jacobi_layout(d.m, d.n, &a.np, &a.ra, &a.rw);
-  size_t smem = in_smem ? jacobi_svd_smem_bytes(d.m, d.n) : jacobi_small_smem_bytes(d.m, d.n);
-  static bool attr_set = false;
-  if (!attr_set) {
-    IPEPS_CUDA_TRY(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        200 * 1024 + 1024));
-    attr_set = true;
-  }
+  jacobi_layout(d.m, d.n, cs, &a.np, &a.ra, &a.rw);
+  const size_t smem = in_smem ? smem_bytes_cs(d.m, d.n, cs) : small_smem_bytes_cs(d.m, d.n, cs);
   a.flops = prof_device_flops();
   // dot-product lanes per pair: about 4 rows per lane, 4..32 lanes
   a.lpp = 4;
   while (a.lpp < 32 && a.lpp * 4 < a.ra) a.lpp *= 2;
-  IPEPS_LAUNCH(K_JACOBI, 0, st, jacobi_kernel<<<d.batch * JCS, JTHREADS, smem, st>>>(a));
-  IPEPS_CUDA_TRY(cudaGetLastError());
-  return 0;
+  return cs == JCS_TALL ? launch_jacobi<JCS_TALL>(a, smem, d.batch, st)
+                        : launch_jacobi<JCS>(a, smem, d.batch, st);
 }
 
 }  // namespace ipeps

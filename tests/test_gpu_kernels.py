@@ -94,9 +94,11 @@ def test_gate_matches_oracle(J, V, h, delta):
     assert np.max(np.abs(out - model.gate(J, V, h, delta))) < 1e-14
 
 
-@pytest.mark.parametrize("m,n", [(2400, 40), (1300, 100)])
-def test_jacobi_svd_columns_in_global_memory(m, n):
-    """Blocks whose row slices exceed shared memory keep their columns in a global buffer."""
+@pytest.mark.parametrize("m,n", [(2400, 40), (1300, 100), (1000, 100), (2600, 120)])
+def test_jacobi_svd_tall_blocks(m, n):
+    """Tall blocks: 16-CTA clusters (m >= 1024, where the part allows them) and, when the row
+    slices exceed shared memory, columns kept in a global buffer ((1000, 100) on 8-CTA clusters,
+    (2600, 120) on either)."""
     batch = 2
     A = _rand((batch, m, n), 11)
     A[1] = A[1] @ np.diag(np.logspace(0, -10, n))       # graded spectrum
