@@ -21,26 +21,42 @@ def ctm_state(GA, GB, lam):
     return A, B, a
 
 
-def converge_and_measure(GA, GB, lam, env, p, tol, max_sweeps):
+OBS_KEYS = ('nA', 'nB', 'imbalance', 'tauzA', 'tauzB', 'energy', 'purityA')
+
+
+def converge_and_measure(GA, GB, lam, env, p, tol, max_sweeps, probe_sweeps=0):
     """Converge the environment (warm from ``env``, or from the traced start when it is None) and
     measure.  ``c8_margin`` in the result is the smallest ctmrg.cut_margin() over the 16 projector
     computations of the last sweep: how far (in decades) the multiplet decisions at the chi cut
-    were from their thresholds when the readout was taken."""
+    were from their thresholds when the readout was taken.  With ``probe_sweeps`` > 0 a copy of the
+    converged environment is swept that many more times and ``drift`` records the largest change
+    of the observables: a converged readout that drifts away (a degenerate pair at the cut that
+    splits from rounding noise, C8) is not a unique result of the method."""
     A, B, a = ctm_state(GA, GB, lam)
     if env is None:
         env = ctmrg.init_env(a, 2, 2, p['chi'], p['D'])
     log = []
+    cut_rel = p.get('cut_rel', ctmrg.PROJ_CUT_REL)
     env, sweeps, delta = ctmrg.ctmrg(a, env, p['chi'], tol=tol, max_sweeps=max_sweeps,
-                                     cut_rel=p.get('cut_rel', ctmrg.PROJ_CUT_REL), log=log)
+                                     cut_rel=cut_rel, log=log)
     obs = measure.observables(A, B, env, p['J'], p['V'], p['h'], p.get('d_A', 2))
     obs.update(ctm_sweeps=sweeps, ctm_delta=delta, c8_margin=float(min(log[-16:])))
+    if probe_sweeps > 0:
+        e2 = env.copy()
+        drift = 0.0
+        for _ in range(probe_sweeps):
+            e2 = ctmrg.sweep(a, e2, p['chi'], cut_rel)
+            o2 = measure.observables(A, B, e2, p['J'], p['V'], p['h'], p.get('d_A', 2))
+            drift = max(drift, max(abs(o2[k] - obs[k]) for k in OBS_KEYS))
+        obs['drift'] = drift
     return env, obs
 
 
-def run(p, tol=1e-10, max_sweeps=500, callback=None, cold=False):
+def run(p, tol=1e-10, max_sweeps=500, callback=None, cold=False, probe_sweeps=0):
     """Evolve with parameters p (J, V, h, D, chi, order, dt, t_max, meas_every[, d_A, cut_rel]).
 
-    Returns a list of observation dicts at t = 0, meas_every, 2 meas_every, ... t_max.  With
+    Returns a list of observation dicts at t = 0, meas_every, 2 meas_every, ... t_max
+    (``probe_sweeps``: see converge_and_measure).  With
     ``cold`` each dict also holds, under 'cold', the readout converged from the traced start of
     that time's tensors instead of the previous environment.  The cold readout depends only on the
     state; the warm one can also depend on the simple update's gauge (the phases of its singular
@@ -58,10 +74,11 @@ def run(p, tol=1e-10, max_sweeps=500, callback=None, cold=False):
     out = []
     for step in range(n_steps + 1):
         if step % stride == 0:
-            env, obs = converge_and_measure(GA, GB, lam, env, p, tol, max_sweeps)
+            env, obs = converge_and_measure(GA, GB, lam, env, p, tol, max_sweeps, probe_sweeps)
             obs.update(t=step * p['dt'], trunc_err_acc=eps_acc, lam=lam.copy())
             if cold:
-                obs['cold'] = converge_and_measure(GA, GB, lam, None, p, tol, max_sweeps)[1]
+                obs['cold'] = converge_and_measure(GA, GB, lam, None, p, tol, max_sweeps,
+                                                   probe_sweeps)[1]
             out.append(obs)
             if callback is not None:
                 callback(obs)

@@ -20,8 +20,11 @@ sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 from inputs import CONFIG1, CONFIG2  # noqa: E402
 from oracle import evolve  # noqa: E402
 
+# sweeps run past every converged readout to see whether it stays put (evolve.converge_and_measure)
+PROBE = 12
+
 KEYS = ("t", "nA", "nB", "imbalance", "tauzA", "tauzB", "energy", "purityA", "trunc_err_acc",
-        "ctm_sweeps", "ctm_delta", "c8_margin")
+        "ctm_sweeps", "ctm_delta", "c8_margin", "drift")
 
 
 def _dump(path, params, out, seconds):
@@ -40,12 +43,12 @@ def run(name):
     if name == "config1":
         p = dict(CONFIG1)
         t0 = time.time()
-        out = evolve.run(p, tol=p["tol"], cold=True)
+        out = evolve.run(p, tol=p["tol"], cold=True, probe_sweeps=PROBE)
         _dump(os.path.join(HERE, "config1_oracle.json"), p, out, time.time() - t0)
     elif name == "config1cut":
         p = dict(CONFIG1, cut_rel=1e-6)
         t0 = time.time()
-        out = evolve.run(p, tol=p["tol"], cold=True)
+        out = evolve.run(p, tol=p["tol"], cold=True, probe_sweeps=PROBE)
         _dump(os.path.join(HERE, "config1_cut1e-6_oracle.json"), p, out, time.time() - t0)
     elif name.startswith("config2"):
         # "config2" = the full workload; "config2:T" stops at t = T (same trajectory, fewer points);
@@ -57,7 +60,7 @@ def run(name):
             p["h"] = h
             p["t_max"] = t_max
             t0 = time.time()
-            out = evolve.run(p, tol=p["tol"], cold=True,
+            out = evolve.run(p, tol=p["tol"], cold=True, probe_sweeps=PROBE,
                              callback=lambda o: print(name, h, o["t"], o["imbalance"],
                                                       o["cold"]["imbalance"], flush=True))
             _dump(os.path.join(HERE, "config2_h%d_oracle.json" % int(h)), p, out, time.time() - t0)
