@@ -49,9 +49,12 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("native", "reference"), default="native")
     ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--workload", choices=("quench", "ctmrg"), default="quench",
+    ap.add_argument("--workload", choices=("quench", "ctmrg", "sweep"), default="quench",
                     help="quench: the Trotter+CTMRG readout workload (default); ctmrg: the standalone "
-                         "CTMRG contraction benchmark on random tensors")
+                         "CTMRG contraction benchmark on random tensors; sweep: the batched "
+                         "64-instance disorder sweep")
+    ap.add_argument("--sequential", action="store_true",
+                    help="sweep workload: run the (D, chi) groups one after the other")
     ap.add_argument("--D", type=int, default=4, help="ctmrg workload: bond dimension (chi = 2 D^2)")
     ap.add_argument("--precision", choices=("fp64", "split"), default="fp64")
     return ap.parse_args()
@@ -390,12 +393,53 @@ def ctmrg_main(args):
     return 0
 
 
+def sweep_main(args):
+    """Batched disorder sweep (64 instances of mixed D, one handle per (D, chi) group, groups on
+    concurrent streams): `steps` readout intervals of 0.5 from t = 0, wall-clock timed."""
+    import torch
+    from inputs import CONFIG4, config4_points
+    from paper_1910_11359_gb300.sweep import disorder_sweep, group_points
+    import paper_1910_11359_gb300 as pkg
+    prec = pkg.SPLIT_BF16X3 if args.precision == "split" else pkg.FP64
+    pts = config4_points(CONFIG4["n"])
+    conc = not args.sequential
+    for _ in range(args.warmup):                      # handles, t = 0 readout
+        disorder_sweep(pts, 0.0, CONFIG4["meas_every"], dt=CONFIG4["dt"], order=CONFIG4["order"],
+                       precision=prec, concurrent=conc)
+    torch.cuda.synchronize()
+    launches0 = pkg.launch_count()
+    t_max = CONFIG4["meas_every"] * args.steps
+    t0 = time.perf_counter()
+    out = disorder_sweep(pts, t_max, CONFIG4["meas_every"], dt=CONFIG4["dt"], order=CONFIG4["order"],
+                         precision=prec, concurrent=conc)
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    launches = pkg.launch_count() - launches0
+    steps_total = len(pts) * round(t_max / CONFIG4["dt"])
+    line = {"metric": "instance Trotter steps/s", "value": steps_total / sec, "unit": "Trotter steps/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16x3" if prec else "f64", "data": "synthetic",
+            "config": {"workload": "batched disorder sweep, 64 instances, h = linspace(0.5, 16, 64), "
+                                   "V in {0, 1}, D in {2, 3, 4}, chi = 2 D^2, 2nd-order dt = 0.05, "
+                                   "readout every 0.5 (timed from t = 0 to t = %.1f)" % t_max,
+                       "groups": {"D=%d chi=%d" % k: len(v) for k, v in group_points(pts).items()},
+                       "concurrent_groups": conc, "timing": "wall clock around the whole sweep"},
+            "sweep_points_per_hour": len(pts) * 3600.0 / (sec * CONFIG4["t_max"] / t_max),
+            "gpu_launches": int(launches),
+            "imbalance_last": [round(o[-1]["imbalance"], 6) for o in out[:4]]}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_main(args)
     if args.workload == "ctmrg":
         return ctmrg_main(args)
+    if args.workload == "sweep":
+        return sweep_main(args)
     return native_main(args)
 
 

@@ -9,6 +9,7 @@ Workloads (shapes and parameters of the paper's runs, restated for the hard-core
 * CONFIG3 -- standalone CTMRG contraction on random iPEPS tensors (4, D, D, D, D) with i.i.d.
   N(0,1) + i N(0,1) entries scaled to unit largest singular value of the 4 x D^4 matricisation;
   D in {4, 5, 6}, chi = 2 D^2, 20 sweeps.  A uses seed 0, B seed 1.
+* CONFIG4 -- batched disorder sweep of 64 instances of mixed D (config4_points).
 """
 import numpy as np
 
@@ -17,6 +18,21 @@ CONFIG1 = dict(J=1.0, V=1.0, h=5.0, D=2, chi=8, order=1, dt=0.02, t_max=1.0, mea
 CONFIG2 = dict(J=1.0, V=1.0, hs=(1.0, 5.0, 10.0), D=3, chi=18, order=2, dt=0.05, t_max=5.0,
                meas_every=0.25, tol=1e-10)
 CONFIG3 = dict(Ds=(4, 5, 6), sweeps=20, seeds=(0, 1))
+
+
+def config4_points(n=64, seed=4):
+    """Batched disorder sweep: n independent instances, h = linspace(0.5, 16, n), V drawn from
+    {0, 1} and D from {2, 3, 4} (default_rng(seed)), chi = 2 D^2, J = 1; second-order Trotter,
+    dt = 0.05 to t = 4, measured every 0.5."""
+    rng = np.random.default_rng(seed)
+    hs = np.linspace(0.5, 16.0, n)
+    Vs = rng.choice([0.0, 1.0], size=n)
+    Ds = rng.choice([2, 3, 4], size=n)
+    return [dict(J=1.0, V=float(V), h=float(h), D=int(D), chi=2 * int(D) ** 2)
+            for h, V, D in zip(hs, Vs, Ds)]
+
+
+CONFIG4 = dict(n=64, order=2, dt=0.05, t_max=4.0, meas_every=0.5, tol=1e-10)
 
 
 def gaussian_complex(shape, seed):

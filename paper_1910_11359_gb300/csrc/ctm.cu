@@ -513,11 +513,13 @@ int ctm_init_env(Ctx& c) {
 }
 
 // Contraction dispatcher: with precision = split BF16x3, products of at least kSplitMinWork complex
-// multiply-adds run on the tensor cores; everything else (and the FP64 path) uses the FP64 GEMM.
-constexpr double kSplitMinWork = 1 << 20;
+// multiply-adds per problem run on the tensor cores; everything else (and the FP64 path) uses the
+// FP64 GEMM.  The choice depends on the problem's shape only, never on the batch size, so an
+// instance gets the same arithmetic alone and in any batch.
+constexpr double kSplitMinWork = 1 << 18;
 
 static int contract(Ctx& c, const GemmDesc& g) {
-  if (c.precision == 1 && (double)g.M * g.N * (double)g.K * g.batch >= kSplitMinWork && !g.skip)
+  if (c.precision == 1 && (double)g.M * g.N * (double)g.K >= kSplitMinWork && !g.skip)
     return tc::zgemm_split_bf16(g, c.tcwork, c.tcwork_bytes, c.derr, c.st);
   return zgemm_f64(g, c.st);
 }
@@ -714,13 +716,16 @@ static int left_move(Ctx& c, int f, int x) {
   } else {
     if ((rc = subspace_svd(c, f, x, R, Rt))) return rc;
   }
+  // the projectors themselves are always formed in FP64: P = R~ V S^{-1/2} recovers the small
+  // singular directions through cancellation, which a split product (error ~1e-5 of |R~| |v|)
+  // would swamp for s_j below ~1e-5 s_1
   g = gd(N, chi, N, 2 * B);     // P = R~ Vs
   g.A = Rt; g.sA = N2; g.lda = N; g.B = w.Vs; g.sB = Nc; g.ldb = chi; g.C = w.P; g.sC = Nc; g.ldc = chi;
-  if ((rc = contract(c, g))) return rc;
+  if ((rc = zgemm_f64(g, st))) return rc;
   g = gd(chi, N, N, 2 * B);     // P~ = Us^+ R
   g.opA = OP_C; g.A = w.Us; g.sA = Nc; g.lda = chi;
   g.B = R; g.sB = N2; g.ldb = N; g.C = w.Pt; g.sC = Nc; g.ldc = N;
-  if ((rc = contract(c, g))) return rc;
+  if ((rc = zgemm_f64(g, st))) return rc;
   // absorption: C1' = P~[y-1] (C1 T1)
   g = gd(chi, chi, N, 2 * B);
   g.Aptr = m.c1A; g.lda = N; g.Bptr = m.c1B; g.ldb = chi; g.C = w.C1n; g.sC = chi2; g.ldc = chi;

@@ -4,6 +4,7 @@
     python tests/golden/make_golden.py config1cut   -> tests/golden/config1_cut1e-6_oracle.json
     python tests/golden/make_golden.py config2      -> tests/golden/config2_h{1,5,10}_oracle.json
     python tests/golden/make_golden.py config2@5    -> tests/golden/config2_h5_oracle.json only
+    python tests/golden/make_golden.py config2:2@5  -> the same, stopped at t = 2
 
 Workloads: inputs.CONFIG1 (D=2, chi=8, first order dt=0.02 to t=1, measured every 0.1) and
 inputs.CONFIG2 (D=3, chi=18, second order dt=0.05 to t=5, measured every 0.25, h in {1,5,10}).
@@ -53,8 +54,9 @@ def run(name):
     elif name.startswith("config2"):
         # "config2" = the full workload; "config2:T" stops at t = T (same trajectory, fewer points);
         # "config2@H" writes only the instance with h = H (the instances are independent)
-        t_max = float(name.split(":")[1]) if ":" in name else CONFIG2["t_max"]
-        hs = [float(name.split("@")[1])] if "@" in name else CONFIG2["hs"]
+        base, _, only = name.partition("@")
+        t_max = float(base.split(":")[1]) if ":" in base else CONFIG2["t_max"]
+        hs = [float(only)] if only else CONFIG2["hs"]
         for h in hs:
             p = {k: v for k, v in CONFIG2.items() if k != "hs"}
             p["h"] = h

@@ -1,0 +1,38 @@
+"""Batched disorder sweep (grouped handles on concurrent streams).
+
+FP64: every instance's readouts must not depend on the company it is batched with (the batched
+run against the same points run one at a time).  Split precision: the imbalance curves (the
+quantity the split path is held to, 1e-4 absolute) against the FP64 sweep."""
+import pytest
+
+pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+POINTS = [dict(J=1.0, V=1.0, h=2.0, D=2, chi=8), dict(J=1.0, V=0.0, h=7.0, D=3, chi=18),
+          dict(J=1.0, V=1.0, h=12.0, D=2, chi=8), dict(J=1.0, V=0.0, h=0.5, D=2, chi=8),
+          dict(J=1.0, V=1.0, h=4.0, D=3, chi=18)]
+KEYS = ("imbalance", "nA", "nB", "energy", "purityA", "trunc_err_acc")
+
+
+def test_batched_sweep_matches_solo_runs_fp64():
+    from paper_1910_11359_gb300.sweep import disorder_sweep
+    batched = disorder_sweep(POINTS, t_max=0.3, meas_every=0.1, precision=0, concurrent=True)
+    worst = 0.0
+    for i, p in enumerate(POINTS):
+        solo = disorder_sweep([p], t_max=0.3, meas_every=0.1, precision=0, concurrent=False)[0]
+        assert len(solo) == len(batched[i]) == 4
+        for a, b in zip(solo, batched[i]):
+            worst = max(worst, max(abs(a[k] - b[k]) for k in KEYS))
+    print("batched vs solo, FP64: max abs difference %.1e" % worst)
+    assert worst < 1e-9
+    assert abs(batched[0][-1]["imbalance"] - 1.0) > 1e-2        # the evolution happened
+
+
+def test_batched_split_sweep_imbalance_vs_fp64():
+    from paper_1910_11359_gb300.sweep import disorder_sweep
+    ref = disorder_sweep(POINTS, t_max=0.3, meas_every=0.1, precision=0, concurrent=True)
+    split = disorder_sweep(POINTS, t_max=0.3, meas_every=0.1, precision=1, concurrent=True)
+    worst = max(abs(a[k] - b[k]) for i in range(len(POINTS)) for a, b in zip(ref[i], split[i])
+                for k in ("imbalance", "nA", "nB"))
+    print("split vs FP64 sweep: max abs difference of imbalance, nA, nB %.1e" % worst)
+    assert worst < 1e-4
