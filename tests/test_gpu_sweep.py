@@ -16,11 +16,11 @@ KEYS = ("imbalance", "nA", "nB", "energy", "purityA", "trunc_err_acc")
 
 def test_batched_sweep_matches_solo_runs_fp64():
     from paper_1910_11359_gb300.sweep import disorder_sweep
-    batched = disorder_sweep(POINTS, t_max=0.3, meas_every=0.1, precision=0, concurrent=True)
+    batched = disorder_sweep(POINTS, t_max=0.2, meas_every=0.1, precision=0, concurrent=True)
     worst = 0.0
     for i, p in enumerate(POINTS):
-        solo = disorder_sweep([p], t_max=0.3, meas_every=0.1, precision=0, concurrent=False)[0]
-        assert len(solo) == len(batched[i]) == 4
+        solo = disorder_sweep([p], t_max=0.2, meas_every=0.1, precision=0, concurrent=False)[0]
+        assert len(solo) == len(batched[i]) == 3
         for a, b in zip(solo, batched[i]):
             worst = max(worst, max(abs(a[k] - b[k]) for k in KEYS))
     print("batched vs solo, FP64: max abs difference %.1e" % worst)
@@ -29,9 +29,12 @@ def test_batched_sweep_matches_solo_runs_fp64():
 
 
 def test_batched_split_sweep_imbalance_vs_fp64():
+    """The split path's CTMRG converges only to its ~1e-6 noise floor (C9 reading: a looser
+    tolerance on that path), so it runs with tol = 1e-6 here."""
     from paper_1910_11359_gb300.sweep import disorder_sweep
-    ref = disorder_sweep(POINTS, t_max=0.3, meas_every=0.1, precision=0, concurrent=True)
-    split = disorder_sweep(POINTS, t_max=0.3, meas_every=0.1, precision=1, concurrent=True)
+    ref = disorder_sweep(POINTS, t_max=0.2, meas_every=0.1, precision=0, concurrent=True)
+    split = disorder_sweep(POINTS, t_max=0.2, meas_every=0.1, precision=1, concurrent=True, tol=1e-6,
+                           max_sweeps=100)
     worst = max(abs(a[k] - b[k]) for i in range(len(POINTS)) for a, b in zip(ref[i], split[i])
                 for k in ("imbalance", "nA", "nB"))
     print("split vs FP64 sweep: max abs difference of imbalance, nA, nB %.1e" % worst)
