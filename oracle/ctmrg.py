@@ -222,12 +222,14 @@ def projectors(R, Rt, chi, cut_rel=PROJ_CUT_REL, log=None):
     """Full-SVD projectors for the bond joining R (columns) and R~ (rows); returns (P, P~, s).
 
     s is the full singular spectrum of M = R R~ (for diagnostics).  When ``log`` is a list it
-    receives cut_margin() of this cut."""
+    receives (cut_margin() of this cut, s_K / s_1 for the largest value the multiplet rule moved
+    out of the kept set where the cutoff would have kept it, else 0)."""
     M = R @ Rt
     U, s, Vh = np.linalg.svd(M)
-    if log is not None:
-        log.append(cut_margin(s, chi, cut_rel))
     K = truncation_rank(s, chi, degen_abs=PROJ_DEGEN_ABS)
+    if log is not None:
+        moved = s[0] > 0 and K < min(chi, len(s)) and s[K] > cut_rel * s[0]
+        log.append((cut_margin(s, chi, cut_rel), float(s[K] / s[0]) if moved else 0.0))
     K = min(K, int(np.sum(s > cut_rel * s[0]))) if s[0] > 0 else 0
     K = max(K, 1) if s[0] > 0 else 0
     N = R.shape[1]

@@ -21,14 +21,22 @@ def ctm_state(GA, GB, lam):
     return A, B, a
 
 
+PROBE_NOISE = 1e-12
+PROBE_SEED = 12345
+
+
 def converge_and_measure(GA, GB, lam, env, p, tol, max_sweeps, probe_sweeps=0):
     """Converge the environment (warm from ``env``, or from the traced start when it is None) and
     measure.  ``c8_margin`` in the result is the smallest ctmrg.cut_margin() over the 16 projector
     computations of the last sweep: how far (in decades) the multiplet decisions at the chi cut
-    were from their thresholds when the readout was taken.  With ``probe_sweeps`` > 0 a copy of the
+    were from their thresholds when the readout was taken; ``c8_level`` is the largest s_K / s_1
+    the multiplet rule moved out of the kept set there (0 when it moved nothing): a readout that
+    depends on keeping or dropping a multiplet of that size is one of several correct ones (C8).  With ``probe_sweeps`` > 0 a copy of the
     converged environment is swept that many more times and ``drift`` records the largest change
     of the one-site observables (occupations, imbalance, purity of rho_A): a converged readout that drifts away (a degenerate pair at the cut that
-    splits from rounding noise, C8) is not a unique result of the method."""
+    splits from rounding noise, C8) is not a unique result of the method.  The copy is first
+    perturbed by a seeded relative 1e-12, so that the probe does not depend on whether this
+    machine's rounding happens to break the symmetry."""
     A, B, a = ctm_state(GA, GB, lam)
     if env is None:
         env = ctmrg.init_env(a, 2, 2, p['chi'], p['D'])
@@ -37,9 +45,20 @@ def converge_and_measure(GA, GB, lam, env, p, tol, max_sweeps, probe_sweeps=0):
     env, sweeps, delta = ctmrg.ctmrg(a, env, p['chi'], tol=tol, max_sweeps=max_sweeps,
                                      cut_rel=cut_rel, log=log)
     obs = measure.observables(A, B, env, p['J'], p['V'], p['h'], p.get('d_A', 2))
-    obs.update(ctm_sweeps=sweeps, ctm_delta=delta, c8_margin=float(min(log[-16:])))
+    last = log[-16:]
+    obs.update(ctm_sweeps=sweeps, ctm_delta=delta, c8_margin=float(min(m for m, _ in last)),
+               c8_level=float(max(v for _, v in last)))
     if probe_sweeps > 0:
+        # seeded relative perturbation of 1e-12, so that an unstable fixed point (whose symmetric
+        # directions this machine's rounding may happen to preserve) shows up deterministically
+        rng = np.random.default_rng(PROBE_SEED)
         e2 = env.copy()
+        for group in (e2.C, e2.T):
+            for tens in group:
+                for key in sorted(tens):
+                    t = tens[key]
+                    noise = rng.standard_normal(t.shape) + 1j * rng.standard_normal(t.shape)
+                    tens[key] = t + PROBE_NOISE * np.abs(t).max() * noise
         for _ in range(probe_sweeps):
             e2 = ctmrg.sweep(a, e2, p['chi'], cut_rel)
         before, after = _site_obs(A, B, env, p), _site_obs(A, B, e2, p)

@@ -22,10 +22,10 @@ from inputs import CONFIG1, CONFIG2  # noqa: E402
 from oracle import evolve  # noqa: E402
 
 # sweeps run past every converged readout to see whether it stays put (evolve.converge_and_measure)
-PROBE = 12
+PROBE = 25
 
 KEYS = ("t", "nA", "nB", "imbalance", "tauzA", "tauzB", "energy", "purityA", "trunc_err_acc",
-        "ctm_sweeps", "ctm_delta", "c8_margin", "drift")
+        "ctm_sweeps", "ctm_delta", "c8_margin", "c8_level", "drift")
 
 
 def _dump(path, params, out, seconds):

@@ -103,8 +103,9 @@ def _compare_rows(out, lam, g, keys, cold=False):
     cold readouts agree (at some times the truncated CTMRG has several fixed points and the
     previous environment, whose gauge follows the simple update's singular-vector phases, selects
     one).  Rows whose multiplet decisions at the chi cut sat within two decades of the rule's
-    thresholds (c8_margin < 2), or whose readout drifts by more than 1e-9 when the oracle keeps
-    sweeping (drift), are not unique either.  Unique rows are held to _row_tol, the others
+    thresholds (c8_margin < 2), that dropped a multiplet above 1e-7 of the largest value there
+    (c8_level), or whose readout drifts by more than 1e-9 when the oracle keeps sweeping (drift),
+    are not unique either.  Unique rows are held to _row_tol, the others
     to 1e-3.  The simple-update state
     (discarded weight; bond spectra of the last row run) at 1e-10 relative / absolute."""
     errs = []
@@ -116,6 +117,8 @@ def _compare_rows(out, lam, g, keys, cold=False):
         # C8: a multiplet decision at the chi cut within two decades of its threshold can go
         # either way under rounding, and each way leads to a valid (different) readout
         unique = unique and ref.get("c8_margin", 99.0) >= 2.0
+        # a readout that depends on dropping a multiplet above 1e-7 s_1 at the cut (C8)
+        unique = unique and ref.get("c8_level", 0.0) <= 1e-7
         # a readout that moves when the oracle keeps sweeping (a degenerate pair at the cut splitting
         # from rounding noise) is likewise not unique
         unique = unique and ref.get("drift", 0.0) < 1e-9
