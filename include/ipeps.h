@@ -93,7 +93,9 @@ ipeps_status ipeps_trotter_step(ipeps_h h, int n_steps, double* trunc_err_out);
  * sweeps until the normalised corner spectra change by less than tol, or until that change has
  * stalled at its rounding floor (no factor-2 improvement of its best value for 10 sweeps while the
  * best is below 1e-7); converged instances stop updating; at most max_sweeps sweeps.  tol <= 0 runs
- * exactly max_sweeps sweeps.  The first call starts from the traced
+ * exactly max_sweeps sweeps.  With precision IPEPS_SPLIT_BF16X3 the contractions leave a noise floor
+ * near 1e-6 in the spectra: a positive tol below 1e-7 is raised to 1e-7 and the stall rule applies
+ * once the best change is below 1e-5.  The first call starts from the traced
  * double layers, later calls from the previous environment.  sweeps_out: host int[batch] or NULL;
  * delta_out: host double[batch] or NULL (last change).  Returns IPEPS_ENOCONV when an instance
  * reached max_sweeps without converging (its environment is still usable). */

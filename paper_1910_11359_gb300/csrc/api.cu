@@ -308,7 +308,9 @@ ipeps_status ctmrg_converge(ipeps_h h, double tol, int max_sweeps, int* sweeps_o
   cudaMemsetAsync(c.w.sweeps, 0, sizeof(int) * B, c.st);
   if ((rc = ctm_spectra(c, tol, 1))) return from_rc(h, rc);
   std::vector<int> frozen(B, 0);
-  const double tol_eff = tol > 0.0 ? tol : -1.0;
+  // split precision: its contractions leave a noise floor near 1e-6 in the corner spectra, so a
+  // requested tolerance below 1e-7 is raised to 1e-7 (the stall rule covers the rest)
+  const double tol_eff = tol > 0.0 ? (c.precision == 1 && tol < 1e-7 ? 1e-7 : tol) : -1.0;
   for (int s = 0; s < max_sweeps; ++s) {
     if ((rc = ctm_sweep(c))) return from_rc(h, rc);
     if ((rc = ctm_spectra(c, tol_eff, 0))) return from_rc(h, rc);

@@ -444,12 +444,14 @@ __global__ void normalize_store_kernel(const cplx* C1n, const cplx* T4n, const c
 // first != 0 only records the spectra of the starting environment.  An instance is frozen (its
 // environment no longer updated) once delta < tol, or once delta has stalled at its rounding floor:
 // no factor-2 improvement of the best delta for kStallWindow sweeps while that best is below
-// kStallMax ("sufficiently well converged", Appendix).  tol <= 0 never freezes.
+// stall_max ("sufficiently well converged", Appendix): kStallMax on the FP64 path,
+// kStallMaxSplit on the split path, whose contractions leave a noise floor near 1e-6.
+// tol <= 0 never freezes.
 constexpr int kStallWindow = 10;
-constexpr double kStallMax = 1e-7;
+constexpr double kStallMax = 1e-7, kStallMaxSplit = 1e-5;
 
 __global__ void spectra_delta_kernel(const double* cs, double* prev, int B, int chi, int first,
-                                     double tol, double* delta, int* frozen, int* sweeps,
+                                     double tol, double stall_max, double* delta, int* frozen, int* sweeps,
                                      double* best, int* since) {
   const int b = blockIdx.x;
   __shared__ double dmax[16];
@@ -490,7 +492,7 @@ __global__ void spectra_delta_kernel(const double* cs, double* prev, int B, int 
   } else {
     since[b] += 1;
   }
-  if (tol > 0.0 && since[b] >= kStallWindow && best[b] < kStallMax) frozen[b] = 1;
+  if (tol > 0.0 && since[b] >= kStallWindow && best[b] < stall_max) frozen[b] = 1;
 }
 
 // ----------------------------------------------------------------------------- drivers
@@ -782,7 +784,8 @@ int ctm_spectra(Ctx& c, double tol, int first) {
   sd.tol = 4e-16 * c.chi; sd.max_sweeps = 80; sd.err = c.derr; sd.sweeps_out = nullptr; sd.skip = nullptr;
   if (int rc = jacobi_svd(sd, c.st)) return rc;
   IPEPS_LAUNCH(K_SPECTRA, 0, c.st,
-               spectra_delta_kernel<<<c.B, 32, 0, c.st>>>(c.w.cs, c.w.prev, c.B, c.chi, first, tol, c.w.delta,
+               spectra_delta_kernel<<<c.B, 32, 0, c.st>>>(c.w.cs, c.w.prev, c.B, c.chi, first, tol,
+                                                          c.precision == 1 ? kStallMaxSplit : kStallMax, c.w.delta,
                                                           c.w.frozen, c.w.sweeps, c.w.best, c.w.since));
   IPEPS_CUDA_TRY(cudaGetLastError());
   return 0;
