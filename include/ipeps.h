@@ -47,7 +47,9 @@ typedef struct {
   int chi;                  /* environment bond dimension (>= D^2, Appendix) */
   int trotter_order;        /* 1 or 2 */
   double dt;                /* Trotter step */
-  int precision;            /* IPEPS_FP64, or a split-precision contraction mode */
+  int precision;            /* IPEPS_FP64 or IPEPS_SPLIT_BF16X3 (contractions on the tensor cores,
+                               FP64 projectors); IPEPS_SPLIT_TF32X3 is declared but this build
+                               returns IPEPS_EUNSUPPORTED for it */
   unsigned long long seed;  /* seeds random starting vectors of iterative solvers */
   const double* J;          /* [batch] hopping, host, copied */
   const double* V;          /* [batch] nearest-neighbour interaction, host, copied */

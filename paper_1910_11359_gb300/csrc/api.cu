@@ -64,9 +64,13 @@ ipeps_status validate(const ipeps_params* p, std::string* why) {
   if (p->chi > 2048) { *why = "chi above 2048 is not supported"; return IPEPS_EUNSUPPORTED; }
   if (p->trotter_order != 1 && p->trotter_order != 2) { *why = "trotter_order must be 1 or 2"; return IPEPS_EINVAL; }
   if (!(p->dt > 0.0)) { *why = "dt must be > 0"; return IPEPS_EINVAL; }
+  if (p->precision == IPEPS_SPLIT_TF32X3) {
+    *why = "IPEPS_SPLIT_TF32X3 is not implemented in this build (use IPEPS_SPLIT_BF16X3)";
+    return IPEPS_EUNSUPPORTED;
+  }
   if (p->precision != IPEPS_FP64 && p->precision != IPEPS_SPLIT_BF16X3) {
     *why = "precision must be IPEPS_FP64 or IPEPS_SPLIT_BF16X3";
-    return IPEPS_EUNSUPPORTED;
+    return IPEPS_EINVAL;
   }
   if (!p->J || !p->V || !p->h) { *why = "J, V, h arrays are required"; return IPEPS_EINVAL; }
   const int N = p->chi * p->D * p->D;

@@ -1,0 +1,70 @@
+"""The C ABI on a machine without a GPU: the library builds, loads, exports every function that
+include/*.h declares, and its host-side logic (argument validation, footprint sizing for
+admission, error reporting) works before any device call."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared(header):
+    text = open(os.path.join(ROOT, "include", header)).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b((?:ipeps|ctmrg)_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1910_11359_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+@pytest.mark.parametrize("header", ["ipeps.h", "ipeps_kernels.h"])
+def test_every_declared_function_is_exported(lib, header):
+    names = _declared(header)
+    assert len(names) >= 8
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def _params(**kw):
+    import paper_1910_11359_gb300._lib as L
+    p = dict(J=[1.0, 1.0], V=[1.0, 0.0], h=[5.0, 2.0], D=3, chi=18, order=2, dt=0.05, precision=0,
+             seed=0)
+    p.update(kw)
+    return L._params(p["J"], p["V"], p["h"], p["D"], p["chi"], p["order"], p["dt"], p["precision"],
+                     p["seed"])
+
+
+def test_footprint_sizing_without_device():
+    import paper_1910_11359_gb300 as pkg
+    one = pkg.footprint_bytes([1.0], [1.0], [5.0], D=3, chi=18)
+    three = pkg.footprint_bytes([1.0] * 3, [1.0] * 3, [1.0, 5.0, 10.0], D=3, chi=18)
+    big = pkg.footprint_bytes([1.0], [1.0], [5.0], D=4, chi=32)
+    split = pkg.footprint_bytes([1.0], [1.0], [5.0], D=4, chi=32, precision=pkg.SPLIT_BF16X3)
+    assert 0 < one < three < 3.5 * one          # per-instance arrays plus shared tables
+    assert big > 2 * one
+    assert split > big                           # the tensor-core operand workspace
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(chi=4), 1),                 # chi < D^2
+    (dict(order=3), 1),               # Trotter order
+    (dict(D=0), 1),
+    (dict(precision=7), 1),
+    (dict(precision=2), 8),           # TF32x3: declared, not implemented in this build
+    (dict(chi=4096), 8),              # beyond the supported chi
+])
+def test_invalid_parameters_are_rejected_before_any_device_call(lib, kw, status):
+    import paper_1910_11359_gb300._lib as L
+    p, keep = _params(**kw)
+    h = ctypes.c_void_p(None)
+    rc = L.lib().ipeps_init(ctypes.byref(p), None, ctypes.byref(h))
+    assert rc == status
+    assert not h.value
+    msg = L.lib().ipeps_last_error(None)
+    assert msg and len(msg) > 5
