@@ -326,14 +326,14 @@ def ctmrg_main(args):
     per step from the traced start."""
     import torch
     import paper_1910_11359_gb300 as pkg
-    from inputs import config3_tensors
+    from inputs import random_ctmrg_tensors
 
     D = args.D
     chi = 2 * D * D
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     stream = torch.cuda.Stream()
     prec = pkg.SPLIT_BF16X3 if args.precision == "split" else pkg.FP64
-    A, B = config3_tensors(D)
+    A, B = random_ctmrg_tensors(D)
     sim = pkg.IPEPS([1.0], [1.0], [5.0], D=D, chi=chi, order=2, dt=0.05, precision=prec,
                     stream=stream.cuda_stream)
     sim.set_tensors(A[None], B[None], None)
@@ -397,25 +397,25 @@ def sweep_main(args):
     """Batched disorder sweep (64 instances of mixed D, one handle per (D, chi) group, groups on
     concurrent streams): `steps` readout intervals of 0.5 from t = 0, wall-clock timed."""
     import torch
-    from inputs import CONFIG4, config4_points
+    from inputs import DISORDER_SWEEP, disorder_sweep_points
     from paper_1910_11359_gb300.sweep import disorder_sweep, group_points
     import paper_1910_11359_gb300 as pkg
     prec = pkg.SPLIT_BF16X3 if args.precision == "split" else pkg.FP64
-    pts = config4_points(CONFIG4["n"])
+    pts = disorder_sweep_points(DISORDER_SWEEP["n"])
     conc = not args.sequential
     for _ in range(args.warmup):                      # handles, t = 0 readout
-        disorder_sweep(pts, 0.0, CONFIG4["meas_every"], dt=CONFIG4["dt"], order=CONFIG4["order"],
+        disorder_sweep(pts, 0.0, DISORDER_SWEEP["meas_every"], dt=DISORDER_SWEEP["dt"], order=DISORDER_SWEEP["order"],
                        precision=prec, concurrent=conc)
     torch.cuda.synchronize()
     launches0 = pkg.launch_count()
-    t_max = CONFIG4["meas_every"] * args.steps
+    t_max = DISORDER_SWEEP["meas_every"] * args.steps
     t0 = time.perf_counter()
-    out = disorder_sweep(pts, t_max, CONFIG4["meas_every"], dt=CONFIG4["dt"], order=CONFIG4["order"],
+    out = disorder_sweep(pts, t_max, DISORDER_SWEEP["meas_every"], dt=DISORDER_SWEEP["dt"], order=DISORDER_SWEEP["order"],
                          precision=prec, concurrent=conc)
     torch.cuda.synchronize()
     sec = time.perf_counter() - t0
     launches = pkg.launch_count() - launches0
-    steps_total = len(pts) * round(t_max / CONFIG4["dt"])
+    steps_total = len(pts) * round(t_max / DISORDER_SWEEP["dt"])
     line = {"metric": "instance Trotter steps/s", "value": steps_total / sec, "unit": "Trotter steps/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -425,7 +425,7 @@ def sweep_main(args):
                                    "readout every 0.5 (timed from t = 0 to t = %.1f)" % t_max,
                        "groups": {"D=%d chi=%d" % k: len(v) for k, v in group_points(pts).items()},
                        "concurrent_groups": conc, "timing": "wall clock around the whole sweep"},
-            "sweep_points_per_hour": len(pts) * 3600.0 / (sec * CONFIG4["t_max"] / t_max),
+            "sweep_points_per_hour": len(pts) * 3600.0 / (sec * DISORDER_SWEEP["t_max"] / t_max),
             "gpu_launches": int(launches),
             "imbalance_last": [round(o[-1]["imbalance"], 6) for o in out[:4]]}
     print(json.dumps(line))

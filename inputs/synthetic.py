@@ -2,25 +2,25 @@
 
 Workloads (shapes and parameters of the paper's runs, restated for the hard-core boson form):
 
-* CONFIG1 -- d = 4 (boson x aux spin-1/2), D = 2, chi = 8, J = V = 1, h = 5, first-order Trotter,
+* QUENCH_D2 -- d = 4 (boson x aux spin-1/2), D = 2, chi = 8, J = V = 1, h = 5, first-order Trotter,
   dt = 0.02 to t = 1, CTMRG to 1e-10, measured every 0.1.
-* CONFIG2 -- D = 3, chi = 18, J = V = 1, h in {1, 5, 10}, second-order Trotter, dt = 0.05 to t = 5,
+* QUENCH_D3 -- D = 3, chi = 18, J = V = 1, h in {1, 5, 10}, second-order Trotter, dt = 0.05 to t = 5,
   measured every 0.25.
-* CONFIG3 -- standalone CTMRG contraction on random iPEPS tensors (4, D, D, D, D) with i.i.d.
+* RANDOM_CTMRG -- standalone CTMRG contraction on random iPEPS tensors (4, D, D, D, D) with i.i.d.
   N(0,1) + i N(0,1) entries scaled to unit largest singular value of the 4 x D^4 matricisation;
   D in {4, 5, 6}, chi = 2 D^2, 20 sweeps.  A uses seed 0, B seed 1.
-* CONFIG4 -- batched disorder sweep of 64 instances of mixed D (config4_points).
+* DISORDER_SWEEP -- batched disorder sweep of 64 instances of mixed D (disorder_sweep_points).
 """
 import numpy as np
 
-CONFIG1 = dict(J=1.0, V=1.0, h=5.0, D=2, chi=8, order=1, dt=0.02, t_max=1.0, meas_every=0.1,
+QUENCH_D2 = dict(J=1.0, V=1.0, h=5.0, D=2, chi=8, order=1, dt=0.02, t_max=1.0, meas_every=0.1,
                tol=1e-10)
-CONFIG2 = dict(J=1.0, V=1.0, hs=(1.0, 5.0, 10.0), D=3, chi=18, order=2, dt=0.05, t_max=5.0,
+QUENCH_D3 = dict(J=1.0, V=1.0, hs=(1.0, 5.0, 10.0), D=3, chi=18, order=2, dt=0.05, t_max=5.0,
                meas_every=0.25, tol=1e-10)
-CONFIG3 = dict(Ds=(4, 5, 6), sweeps=20, seeds=(0, 1))
+RANDOM_CTMRG = dict(Ds=(4, 5, 6), sweeps=20, seeds=(0, 1))
 
 
-def config4_points(n=64, seed=4):
+def disorder_sweep_points(n=64, seed=4):
     """Batched disorder sweep: n independent instances, h = linspace(0.5, 16, n), V drawn from
     {0, 1} and D from {2, 3, 4} (default_rng(seed)), chi = 2 D^2, J = 1; second-order Trotter,
     dt = 0.05 to t = 4, measured every 0.5."""
@@ -32,7 +32,7 @@ def config4_points(n=64, seed=4):
             for h, V, D in zip(hs, Vs, Ds)]
 
 
-CONFIG4 = dict(n=64, order=2, dt=0.05, t_max=4.0, meas_every=0.5, tol=1e-10)
+DISORDER_SWEEP = dict(n=64, order=2, dt=0.05, t_max=4.0, meas_every=0.5, tol=1e-10)
 
 
 def gaussian_complex(shape, seed):
@@ -41,7 +41,7 @@ def gaussian_complex(shape, seed):
     return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
 
 
-def config3_tensors(D, d=4, seeds=(0, 1)):
+def random_ctmrg_tensors(D, d=4, seeds=(0, 1)):
     """Random site tensors A, B of shape (d, D, D, D, D), each with unit largest singular value
     of its d x D^4 matricisation."""
     out = []

@@ -10,7 +10,7 @@ generators, which hold none of the method's arithmetic.
 What the oracle computes (all complex128 / float64, LAPACK via NumPy for SVD and eigh):
 
 * ``model``   -- local operators of the dilated site (hard-core boson x auxiliary spin-1/2), the
-  bond Hamiltonian and its Trotter gate (Sec. "Set up for iPEPS", Eq. Hanc, in BASELINE's
+  bond Hamiltonian and its Trotter gate (Sec. "Set up for iPEPS", Eq. Hanc, written in
   hard-core-boson form), the CDW (x) |+> initial product state (Sec. "Set up for iPEPS",
   Initialization; Fig. 1).
 * ``su``      -- the simple update of Jiang, Weng & Xiang (PRL 101, 090603 (2008)), cited by the

@@ -37,7 +37,7 @@ below cut_rel of the largest are dropped (pseudo-inverse); the kept rank is zero
 paper fixes no cutoff; the default PROJ_CUT_REL = 1e-10 keeps the early-time physics (a cutoff of
 1e-6 biases I(t = 0.01) by 6e-7).  Rounding in the singular vectors of M is amplified by about
 eps s_1 / (s_K gap) in the projectors, so when the cut falls in a cluster of tiny singular values the
-fixed point depends on rounding (config-1 workload, t >= 0.7: 1e-8 shifts under a 1e-15 change of the
+fixed point depends on rounding (D = 2 quench workload, t >= 0.7: 1e-8 shifts under a 1e-15 change of the
 gates); a larger cutoff such as 1e-6 removes that sensitivity.
 
 Parity: pinned by tests/test_oracle_ctmrg.py (Ising PEPS against Onsager/Yang, exact dimer states,

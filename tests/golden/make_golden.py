@@ -1,13 +1,13 @@
 """Write the oracle's reference trajectories for the parity tests (calls only oracle/ and inputs/).
 
-    python tests/golden/make_golden.py config1      -> tests/golden/config1_oracle.json
-    python tests/golden/make_golden.py config1cut   -> tests/golden/config1_cut1e-6_oracle.json
-    python tests/golden/make_golden.py config2      -> tests/golden/config2_h{1,5,10}_oracle.json
-    python tests/golden/make_golden.py config2@5    -> tests/golden/config2_h5_oracle.json only
-    python tests/golden/make_golden.py config2:2@5  -> the same, stopped at t = 2
+    python tests/golden/make_golden.py quench_d2      -> tests/golden/quench_d2_oracle.json
+    python tests/golden/make_golden.py quench_d2_cut   -> tests/golden/quench_d2_cut1e-6_oracle.json
+    python tests/golden/make_golden.py quench_d3      -> tests/golden/quench_d3_h{1,5,10}_oracle.json
+    python tests/golden/make_golden.py quench_d3@5    -> tests/golden/quench_d3_h5_oracle.json only
+    python tests/golden/make_golden.py quench_d3:2@5  -> the same, stopped at t = 2
 
-Workloads: inputs.CONFIG1 (D=2, chi=8, first order dt=0.02 to t=1, measured every 0.1) and
-inputs.CONFIG2 (D=3, chi=18, second order dt=0.05 to t=5, measured every 0.25, h in {1,5,10}).
+Workloads: inputs.QUENCH_D2 (D=2, chi=8, first order dt=0.02 to t=1, measured every 0.1) and
+inputs.QUENCH_D3 (D=3, chi=18, second order dt=0.05 to t=5, measured every 0.25, h in {1,5,10}).
 Every stored value is the oracle's; nothing here touches the CUDA path.
 """
 import json
@@ -18,7 +18,7 @@ import time
 HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 
-from inputs import CONFIG1, CONFIG2  # noqa: E402
+from inputs import QUENCH_D2, QUENCH_D3  # noqa: E402
 from oracle import evolve  # noqa: E402
 
 # sweeps run past every converged readout to see whether it stays put (evolve.converge_and_measure)
@@ -41,31 +41,31 @@ def _dump(path, params, out, seconds):
 
 
 def run(name):
-    if name == "config1":
-        p = dict(CONFIG1)
+    if name == "quench_d2":
+        p = dict(QUENCH_D2)
         t0 = time.time()
         out = evolve.run(p, tol=p["tol"], cold=True, probe_sweeps=PROBE)
-        _dump(os.path.join(HERE, "config1_oracle.json"), p, out, time.time() - t0)
-    elif name == "config1cut":
-        p = dict(CONFIG1, cut_rel=1e-6)
+        _dump(os.path.join(HERE, "quench_d2_oracle.json"), p, out, time.time() - t0)
+    elif name == "quench_d2_cut":
+        p = dict(QUENCH_D2, cut_rel=1e-6)
         t0 = time.time()
         out = evolve.run(p, tol=p["tol"], cold=True, probe_sweeps=PROBE)
-        _dump(os.path.join(HERE, "config1_cut1e-6_oracle.json"), p, out, time.time() - t0)
-    elif name.startswith("config2"):
-        # "config2" = the full workload; "config2:T" stops at t = T (same trajectory, fewer points);
-        # "config2@H" writes only the instance with h = H (the instances are independent)
+        _dump(os.path.join(HERE, "quench_d2_cut1e-6_oracle.json"), p, out, time.time() - t0)
+    elif name.startswith("quench_d3"):
+        # "quench_d3" = the full workload; "quench_d3:T" stops at t = T (same trajectory, fewer points);
+        # "quench_d3@H" writes only the instance with h = H (the instances are independent)
         base, _, only = name.partition("@")
-        t_max = float(base.split(":")[1]) if ":" in base else CONFIG2["t_max"]
-        hs = [float(only)] if only else CONFIG2["hs"]
+        t_max = float(base.split(":")[1]) if ":" in base else QUENCH_D3["t_max"]
+        hs = [float(only)] if only else QUENCH_D3["hs"]
         for h in hs:
-            p = {k: v for k, v in CONFIG2.items() if k != "hs"}
+            p = {k: v for k, v in QUENCH_D3.items() if k != "hs"}
             p["h"] = h
             p["t_max"] = t_max
             t0 = time.time()
             out = evolve.run(p, tol=p["tol"], cold=True, probe_sweeps=PROBE,
                              callback=lambda o: print(name, h, o["t"], o["imbalance"],
                                                       o["cold"]["imbalance"], flush=True))
-            _dump(os.path.join(HERE, "config2_h%d_oracle.json" % int(h)), p, out, time.time() - t0)
+            _dump(os.path.join(HERE, "quench_d3_h%d_oracle.json" % int(h)), p, out, time.time() - t0)
     else:
         raise SystemExit("unknown workload " + name)
 

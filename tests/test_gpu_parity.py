@@ -132,9 +132,9 @@ def _compare_rows(out, lam, g, keys, cold=False):
 
 
 @pytest.mark.parametrize("cold", [False, True])
-def test_config1_evolution_matches_golden(cold):
-    """Config-1 workload with the default projector cutoff (1e-10), warm and cold readouts."""
-    g = json.load(open(os.path.join(GOLDEN, "config1_oracle.json")))
+def test_quench_d2_evolution_matches_golden(cold):
+    """D = 2 quench workload with the default projector cutoff (1e-10), warm and cold readouts."""
+    g = json.load(open(os.path.join(GOLDEN, "quench_d2_oracle.json")))
     out, lam = _evolve_like(g, cold=cold)
     errs = _compare_rows(out, lam, g, ("imbalance", "nA", "nB", "tauzA", "tauzB", "energy", "purityA"),
                          cold=cold)
@@ -142,9 +142,9 @@ def test_config1_evolution_matches_golden(cold):
 
 
 @pytest.mark.parametrize("cold", [False, True])
-def test_config1_cutoff_1e6_matches_golden(cold):
+def test_quench_d2_cutoff_1e6_matches_golden(cold):
     """Projector cutoff 1e-6, warm and cold readouts."""
-    g = json.load(open(os.path.join(GOLDEN, "config1_cut1e-6_oracle.json")))
+    g = json.load(open(os.path.join(GOLDEN, "quench_d2_cut1e-6_oracle.json")))
     out, lam = _evolve_like(g, cut_rel=1e-6, cold=cold)
     errs = _compare_rows(out, lam, g, ("imbalance", "nA", "nB", "tauzA", "tauzB", "energy", "purityA"),
                          cold=cold)
@@ -174,29 +174,29 @@ def test_ctmrg_subspace_projectors_fixed_sweeps():
     assert err_s < TOL and err_o < TOL
 
 
-_CONFIG2_HS = (1.0, 5.0, 10.0)
-_CONFIG2_ROWS = 9          # t = 0 .. 2.0 of the t = 5 golden trajectories
+_QUENCH_D3_HS = (1.0, 5.0, 10.0)
+_QUENCH_D3_ROWS = 9          # t = 0 .. 2.0 of the t = 5 golden trajectories
 
 
 @pytest.fixture(scope="module")
-def config2_run():
-    """Config-2 workload (D = 3, chi = 18, second order, h = 1, 5, 10) to t = 2: the three instances
+def quench_d3_run():
+    """D = 3 quench workload (chi = 18, second order, h = 1, 5, 10) to t = 2: the three instances
     run as one batch on the device, once with warm-started and once with cold readouts; each test
     below compares one instance with its oracle trajectory."""
-    paths = [os.path.join(GOLDEN, "config2_h%d_oracle.json" % int(h)) for h in _CONFIG2_HS]
+    paths = [os.path.join(GOLDEN, "quench_d3_h%d_oracle.json" % int(h)) for h in _QUENCH_D3_HS]
     if not all(os.path.exists(q) for q in paths):
-        pytest.skip("config-2 golden trajectories not generated")
+        pytest.skip("D = 3 golden trajectories not generated")
     gs = [json.load(open(q)) for q in paths]
     if not all("cold" in g["rows"][0] for g in gs):
-        pytest.skip("config-2 golden trajectories lack cold readouts")
+        pytest.skip("D = 3 golden trajectories lack cold readouts")
     p = gs[0]["params"]
     stride = int(round(p["meas_every"] / p["dt"]))
     res = {}
     for cold in (False, True):
-        sim = _sim(J=[1.0] * 3, V=[1.0] * 3, h=list(_CONFIG2_HS), D=p["D"], chi=p["chi"],
+        sim = _sim(J=[1.0] * 3, V=[1.0] * 3, h=list(_QUENCH_D3_HS), D=p["D"], chi=p["chi"],
                    order=p["order"], dt=p["dt"])
         outs = []
-        for i in range(_CONFIG2_ROWS):
+        for i in range(_QUENCH_D3_ROWS):
             if i > 0:
                 sim.trotter_step(stride)
             if cold:
@@ -210,7 +210,7 @@ def config2_run():
 
 @pytest.mark.parametrize("cold", [False, True])
 @pytest.mark.parametrize("hi", [0, 1, 2])
-def test_config2_evolution_matches_golden(config2_run, hi, cold):
-    gs, res = config2_run
+def test_quench_d3_evolution_matches_golden(quench_d3_run, hi, cold):
+    gs, res = quench_d3_run
     outs, lam = res[cold]
     _compare_rows([o[hi] for o in outs], lam[hi], gs[hi], ("imbalance", "nA", "nB", "energy"), cold=cold)

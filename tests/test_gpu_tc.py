@@ -85,10 +85,10 @@ def test_split_ctmrg_matches_oracle_d3():
 
 
 def test_split_ctmrg_random_d4_vs_fp64():
-    """Config-3 tensors at D = 4, chi = 32 (N = 512), 4 sweeps: split path against the FP64 path."""
+    """Random tensors at D = 4, chi = 32 (N = 512), 4 sweeps: split path against the FP64 path."""
     import paper_1910_11359_gb300 as pkg
-    from inputs import config3_tensors
-    A, B = config3_tensors(4)
+    from inputs import random_ctmrg_tensors
+    A, B = random_ctmrg_tensors(4)
     res = []
     for prec in (pkg.FP64, pkg.SPLIT_BF16X3):
         sim = pkg.IPEPS([1.0], [1.0], [5.0], D=4, chi=32, order=2, dt=0.05, precision=prec)
