@@ -158,3 +158,31 @@ def test_torus_helper_matches_state_vector():
     rot = (0, 4, 1, 2, 3)
     Tr = {p: t.transpose(rot) for p, t in T.items()}
     assert abs(statevector.one_site(Tr, 2, O, (0, 0)).real - sv) < 1e-12
+
+
+def test_projector_multiplet_rule_and_margin():
+    """The chi-cut rule of the projectors (C8): a relative gap below 1e-10 or an absolute gap below
+    1e-11 s_1 is one multiplet; values under the cutoff are not examined; cut_margin measures the
+    distance of the deciding test from its threshold in decades."""
+    from oracle.su import truncation_rank
+    abs_floor = ctmrg.PROJ_DEGEN_ABS
+    # exact pair at the cut (relative test), well above the floor
+    s = np.array([1.0, 0.3, 0.1, 0.1, 0.05])
+    assert truncation_rank(s, 3, degen_abs=abs_floor) == 2
+    # small pair whose relative gap (1e-6) passes the relative test but whose absolute gap (3e-12)
+    # is below the floor: one multiplet only through the absolute test
+    s = np.array([1.0, 0.5, 3.000003e-6, 3.0e-6, 1e-7])
+    assert truncation_rank(s, 3) == 3
+    assert truncation_rank(s, 3, degen_abs=abs_floor) == 2
+    # a genuine gap is kept
+    s = np.array([1.0, 0.5, 2e-6, 1e-6, 1e-7])
+    assert truncation_rank(s, 3, degen_abs=abs_floor) == 3
+    # margins: an exact pair is far from both thresholds; the cut then stops at the gap 0.3 / 0.1,
+    # whose decision lies log10(0.2 / 1e-11) = 10.3 decades from the absolute threshold
+    assert abs(ctmrg.cut_margin(np.array([1.0, 0.3, 0.1, 0.1, 0.05]), 3) - np.log10(0.2 / 1e-11)) < 1e-9
+    # a gap of 1e-9 s_1 between values ~1e-3: the relative test is 4 decades from its threshold, the
+    # absolute one 2 decades -- the decision (not a multiplet) is 2 decades from flipping
+    m = ctmrg.cut_margin(np.array([1.0, 0.5, 1e-3 + 1e-9, 1e-3, 1e-4]), 3)
+    assert abs(m - 2.0) < 1e-3
+    # below the cutoff nothing is examined
+    assert ctmrg.cut_margin(np.array([1.0, 1e-12, 1e-12, 1e-13]), 2, cut_rel=1e-10) == np.inf
