@@ -87,3 +87,18 @@ def test_warm_and_cold_start_agree():
     o2 = measure.observables(A, B, env_warm, 1.0, 1.0, 5.0)
     for k in ('nA', 'nB', 'energy', 'purityA'):
         assert abs(o1[k] - o2[k]) < 1e-10, k
+
+
+def test_convergence_in_chi_and_d():
+    """P11, the paper's own criterion (Appendix: results are trusted where D vs D+1 and chi vs 2 chi
+    agree).  At D = 2 the readout is converged in chi: chi = 8 and chi = 16 give the same imbalance
+    to 3e-7 up to t = 0.5 (observed 2.2e-7).  In D the simple-update truncation dominates: D = 2
+    and D = 3 agree to 1e-4 at t = 0.1 (observed 4.1e-5) and drift apart afterwards, as the
+    discarded weight of D = 2 (1.7e-2 at t = 0.5 vs 1.1e-4 at D = 3 by t = 0.2) says they should."""
+    base = dict(J=1.0, V=1.0, h=5.0, order=2, dt=0.05, meas_every=0.1)
+    a = evolve.run(dict(base, D=2, chi=8, t_max=0.5))
+    b = evolve.run(dict(base, D=2, chi=16, t_max=0.5))
+    assert max(abs(x["imbalance"] - y["imbalance"]) for x, y in zip(a, b)) < 3e-7
+    c = evolve.run(dict(base, D=3, chi=9, t_max=0.1))
+    assert abs(a[1]["imbalance"] - c[1]["imbalance"]) < 1e-4
+    assert c[-1]["trunc_err_acc"] < a[1]["trunc_err_acc"]
