@@ -50,7 +50,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("native", "reference"), default="native")
     ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--workload", choices=("quench", "ctmrg", "sweep"), default="quench",
+    ap.add_argument("--requests", type=int, default=32, help="serve workload: requests in the stream")
+    ap.add_argument("--workload", choices=("quench", "ctmrg", "sweep", "serve"), default="quench",
                     help="quench: the Trotter+CTMRG readout workload (default); ctmrg: the standalone "
                          "CTMRG contraction benchmark on random tensors; sweep: the batched "
                          "64-instance disorder sweep")
@@ -435,6 +436,40 @@ def sweep_main(args):
     return 0
 
 
+def serve_main(args):
+    """Serving loop: a seeded Poisson stream of quench requests (mean 4 per second, D in 2..4,
+    chi in [D^2, 3 D^2], h in [0.5, 16], V in {0, 0.5, 1}, t_max in {1, 2}, readouts every 0.5),
+    admitted by footprint under half of the free device memory, run on 4 worker streams."""
+    import torch
+    from paper_1910_11359_gb300.serve import LibraryEngine, Server, percentile, poisson_requests
+    import paper_1910_11359_gb300 as pkg
+    prec = pkg.SPLIT_BF16X3 if args.precision == "split" else pkg.FP64
+    reqs = poisson_requests(args.requests, rate=4.0, seed=5, d_choices=(2, 3, 4),
+                            t_max_choices=(1.0, 2.0), precision=prec)
+    free, _ = torch.cuda.mem_get_info()
+    srv = Server(LibraryEngine(tol=1e-10 if prec == pkg.FP64 else 1e-7), budget_bytes=free // 2,
+                 workers=4)
+    launches0 = pkg.launch_count()
+    t0 = time.perf_counter()
+    out = srv.run(reqs)
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    lat = [r.latency for r in out]
+    steps = sum(int(round(r.t_max / r.dt)) for r in out)
+    line = {"metric": "served Trotter steps/s", "value": steps / sec, "unit": "Trotter steps/s",
+            "n_gpus": 1, "steps": len(out), "warmup": 0, "ms_per_step": 1e3 * sec / len(out),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16x3" if prec else "f64", "data": "synthetic",
+            "config": {"workload": "serving loop, %d Poisson requests (mean 4/s), D in 2..4, "
+                                   "chi in [D^2, 3 D^2], t_max in {1, 2}" % len(out),
+                       "budget_bytes": srv.budget, "peak_admitted_bytes": srv.peak_used,
+                       "workers": srv.nworkers, "timing": "wall clock over the whole stream"},
+            "latency_s": {"p50": percentile(lat, 50), "p99": percentile(lat, 99)},
+            "gpu_launches": int(pkg.launch_count() - launches0)}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -443,6 +478,8 @@ def main():
         return ctmrg_main(args)
     if args.workload == "sweep":
         return sweep_main(args)
+    if args.workload == "serve":
+        return serve_main(args)
     return native_main(args)
 
 
