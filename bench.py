@@ -166,6 +166,14 @@ def reference_main(args):
     return 0
 
 
+def latency_summary(step_ms, sweep_ms):
+    """p50 / p99 of the per-step (readout interval) times and of the per-sweep times (a step's time
+    over the CTMRG sweeps it ran: the batch sweeps until its slowest instance converges), at the
+    workload's stated error (FP64, CTMRG to 1e-10)."""
+    return {"step_p50": float(np.percentile(step_ms, 50)), "step_p99": float(np.percentile(step_ms, 99)),
+            "sweep_p50": float(np.percentile(sweep_ms, 50)), "sweep_p99": float(np.percentile(sweep_ms, 99))}
+
+
 # ----------------------------------------------------------------------------- replicas
 def reduce_max_ms(total_ms, dist, device):
     """Max over ranks of a replica's timed region (every rank receives it); no data-path collective
@@ -222,6 +230,8 @@ def native_main(args):
         pkg.profile_enable(True)
         total_ms = 0.0
         sweeps = []
+        step_ms = []
+        sweep_ms = []                                         # per step: time / sweeps run
         last = None
         for _ in range(args.steps):
             flush.fill_(1.0)                                  # L2 flush between timed steps
@@ -231,7 +241,10 @@ def native_main(args):
             last, sw = step()
             e1.record(stream)
             e1.synchronize()
-            total_ms += e0.elapsed_time(e1)
+            ms = e0.elapsed_time(e1)
+            total_ms += ms
+            step_ms.append(ms)
+            sweep_ms.append(ms / max(1, max(int(s) for s in sw)))
             sweeps.extend(int(s) for s in sw)
         torch.cuda.synchronize()
         prof = pkg.profile_read()
@@ -298,6 +311,7 @@ def native_main(args):
                      "traffic": traffic, "launches": n, "avg_launch_us": 1e3 * ms / max(n, 1),
                      "peak_source": "FP64 FMA rate measured in this run (no FP64 tensor path)"},
         "kernel_time_share": shares,
+        "latency_ms": latency_summary(step_ms, sweep_ms),
         "gpu_launches": int(launches),
         "clocks": clk,
         "cpu_baseline": {"value": cpu_rate, "unit": UNIT, "cores": 1, "kind": "oracle",
