@@ -113,8 +113,9 @@ ORACLE_SAMPLE = ("one instance (h=5), 5 second-order Trotter steps from t=0, 2 C
                  "sweeps per readout")
 
 
-def oracle_sample(sweeps_per_readout):
-    """Time the oracle on a bounded sample; returns (steps/s, sample seconds)."""
+def oracle_sample(sweeps_per_readout, threads=1):
+    """Time the oracle on a bounded sample with `threads` BLAS/OpenMP threads; returns (steps/s,
+    sample seconds, parts)."""
     code = r"""
 import json, sys, time
 sys.path.insert(0, %r)
@@ -131,12 +132,13 @@ measure.observables(A, B, env, 1.0, 1.0, 5.0)
 t4 = time.perf_counter()
 print(json.dumps(dict(su=t1 - t0, sweep=(t3 - t2) / 2, measure=t4 - t3, total=t4 - t0)))
 """ % ROOT
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    n = str(int(threads))
+    env = dict(os.environ, OMP_NUM_THREADS=n, OPENBLAS_NUM_THREADS=n, MKL_NUM_THREADS=n)
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
                          timeout=600)
     r = json.loads(out.stdout.strip().splitlines()[-1])
     per_instance = r["su"] + sweeps_per_readout * r["sweep"] + r["measure"]
-    rate = STEPS_PER_READOUT / per_instance          # Trotter steps/s for one instance, one core
+    rate = STEPS_PER_READOUT / per_instance          # Trotter steps/s for one instance
     return rate, r["total"], r
 
 
@@ -296,6 +298,8 @@ def native_main(args):
         return 0
     mean_sweeps = float(np.mean(sweeps)) if sweeps else 10.0
     cpu_rate, cpu_sec, cpu_parts = oracle_sample(mean_sweeps)
+    ncores = os.cpu_count() or 1
+    all_rate, all_sec, _ = oracle_sample(mean_sweeps, threads=ncores)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -316,7 +320,9 @@ def native_main(args):
         "clocks": clk,
         "cpu_baseline": {"value": cpu_rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": ORACLE_SAMPLE, "sample_seconds": round(cpu_sec, 2),
-                         "parts_s": {k: round(v, 3) for k, v in cpu_parts.items()}},
+                         "parts_s": {k: round(v, 3) for k, v in cpu_parts.items()},
+                         "all_cores": {"value": all_rate, "cores": ncores,
+                                       "sample_seconds": round(all_sec, 2)}},
     }
     print(json.dumps(line))
     if dist is not None:
