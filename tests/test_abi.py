@@ -68,3 +68,29 @@ def test_invalid_parameters_are_rejected_before_any_device_call(lib, kw, status)
     assert not h.value
     msg = L.lib().ipeps_last_error(None)
     assert msg and len(msg) > 5
+
+
+def test_null_handles_and_bad_sizes_fail_cleanly(lib):
+    """Every entry point refuses a NULL handle or an impossible size with IPEPS_EINVAL (1) and a
+    message, without touching the device; destroying NULL is a no-op."""
+    vp = ctypes.c_void_p
+    lib.ipeps_last_error.restype = ctypes.c_char_p
+    calls = [
+        lambda: lib.ipeps_set_tensors(vp(None), vp(None), vp(None), vp(None)),
+        lambda: lib.ipeps_trotter_step(vp(None), 1, vp(None)),
+        lambda: lib.ctmrg_reset(vp(None)),
+        lambda: lib.ctmrg_converge(vp(None), ctypes.c_double(1e-10), 10, vp(None), vp(None)),
+        lambda: lib.ipeps_measure(vp(None), vp(None)),
+        lambda: lib.ipeps_corner_spectrum(vp(None), 0, 0, 0, vp(None)),
+        lambda: lib.ipeps_get_lambda(vp(None), vp(None)),
+        lambda: lib.ipeps_get_tensors(vp(None), vp(None), vp(None)),
+        # m < n, and a batch beyond the allocation-free entry point's fixed scratch
+        lambda: lib.ipeps_kernel_svd(3, 5, 1, vp(1), vp(None), vp(1), vp(None), ctypes.c_double(1e-14),
+                                     10, vp(None), vp(None)),
+        lambda: lib.ipeps_kernel_svd_noalloc(8, 8, 5000, vp(1), vp(None), vp(1), vp(None),
+                                             ctypes.c_double(1e-14), 10, vp(None), vp(None)),
+    ]
+    for call in calls:
+        assert call() == 1
+        assert len(lib.ipeps_last_error(vp(None)) or b"") > 5
+    assert lib.ipeps_destroy(vp(None)) == 0
