@@ -29,9 +29,10 @@ int permute_c128(const cplx* in, cplx* out, int rank, const int* dims, const int
                  long long s_in, long long s_out, cudaStream_t st);
 
 // One-sided (Hestenes) Jacobi SVD of a batch of m x n complex matrices (m >= n), A = U S V^+.
-// Each problem is handled by one thread-block cluster whose CTAs own disjoint row slices of [A; W]
-// in shared memory; pair dot products are reduced across the cluster through distributed shared
-// memory.  Singular values are sorted in descending order.  U (m x n, row-major, may be null),
+// Each problem is handled by one thread-block cluster (8 CTAs, or 16 for m >= 1024 where the part
+// accepts that size) whose CTAs own disjoint row slices of [A; W], in shared memory or, when they
+// do not fit, in SvdDesc::gwork; pair dot products are reduced across the cluster through
+// distributed shared memory.  Singular values are sorted in descending order.  U (m x n, row-major, may be null),
 // V (n x n row-major with V[i*ldv + j] = V_ij, may be null).
 struct SvdDesc {
   int m, n, batch;

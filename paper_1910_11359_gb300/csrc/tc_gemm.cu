@@ -5,12 +5,12 @@
 // and each FP64 value x is split into two BF16 terms x ~ hi + lo (hi = bf16(x), lo = bf16(x - hi));
 // the three leading products hi*hi + hi*lo + lo*hi are obtained by tripling K:
 //   A3 = [A_hi | A_hi | A_lo],  B3 = [B_hi ; B_lo ; B_hi]   (K3 = 6K),  C_big = A3 B3,
-// accumulated in FP32.  Operands are prepared K-major (A3 rows x K3, B3^T rows x K3) by elementwise
+// accumulated in FP32.  Operands are prepared K-major (A3 rows x K3, B3^T rows x K3) by tiled
 // kernels; the GEMM kernel below is a plain BF16 x BF16 -> FP32 tcgen05 GEMM:
-//   * one CTA per 128 x 128 output tile, 6 warps: warp 0 issues TMA loads (128B-swizzled 128 x 64
-//     tiles of both operands into a 4-stage ring), warp 1 allocates 128 TMEM columns and one of its
-//     threads issues tcgen05.mma (M = 128, N = 128, K = 16, BF16 in, FP32 accumulator in TMEM),
-//     warps 2..5 read the accumulator with tcgen05.ld and store FP32 rows;
+//   * one CTA per 128 x BN output tile (BN = 128 or 256), 6 warps: warp 0 issues TMA loads
+//     (128B-swizzled 128 x 64 and BN x 64 tiles into a 4-stage ring), warp 1 allocates BN TMEM
+//     columns and one of its threads issues tcgen05.mma (M = 128, N = BN, K = 16, BF16 in, FP32
+//     accumulator in TMEM), warps 2..5 read the accumulator with tcgen05.ld and store FP32 rows;
 //   * full / empty mbarriers per stage (TMA transaction bytes / tcgen05.commit), one more for the
 //     finished accumulator; every wait is bounded: on timeout the CTA raises DEV_TIMEOUT in the
 //     error word, the other roles stop, outstanding TMA loads are drained (bounded) and the TMEM
