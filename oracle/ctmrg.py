@@ -307,7 +307,8 @@ def spectra_delta(s_new, s_old):
 
 
 STALL_WINDOW = 10      # sweeps without a factor-2 improvement of the best delta
-STALL_MAX = 1e-7       # ... counted as a stall only once the best delta is below this
+STALL_MAX = 1e-7       # ... counted as a stall only while the best and the current delta are below this
+STALL_GROWTH = 4.0     # ... and while the current delta is within this factor of the best one
 
 
 def ctmrg(a, env, chi, tol=1e-10, max_sweeps=200, min_sweeps=1, cut_rel=PROJ_CUT_REL,
@@ -316,8 +317,11 @@ def ctmrg(a, env, chi, tol=1e-10, max_sweeps=200, min_sweeps=1, cut_rel=PROJ_CUT
 
     The paper asks for a "sufficiently well-converged" environment (Appendix).  Reading: stop at
     delta < tol, or when delta has stalled at its rounding floor -- no factor-2 improvement of the
-    best delta for ``stall_window`` sweeps while that best is already below ``stall_max``.  With
-    tol <= 0 exactly max_sweeps sweeps run (no stall test)."""
+    best delta for ``stall_window`` sweeps while that best is already below ``stall_max`` and the
+    current delta still sits at that floor (below ``stall_max`` and within a factor
+    ``STALL_GROWTH`` of the best).  A delta that grows again after coming close to a fixed point
+    means the run is leaving an unstable fixed point, not sitting at a rounding floor; such a run
+    goes on sweeping.  With tol <= 0 exactly max_sweeps sweeps run (no stall test)."""
     prev = corner_spectra(env, chi)
     delta = np.inf
     best, since = np.inf, 0
@@ -333,7 +337,8 @@ def ctmrg(a, env, chi, tol=1e-10, max_sweeps=200, min_sweeps=1, cut_rel=PROJ_CUT
             best, since = delta, 0
         else:
             since += 1
-        if tol > 0 and since >= stall_window and best < stall_max:
+        if (tol > 0 and since >= stall_window and best < stall_max and delta < stall_max
+                and delta <= STALL_GROWTH * best):
             break
     return env, n, delta
 

@@ -21,7 +21,7 @@ def ctm_state(GA, GB, lam):
     return A, B, a
 
 
-PROBE_NOISE = 1e-12
+PROBE_NOISE = 1e-6
 PROBE_SEED = 12345
 
 
@@ -31,12 +31,18 @@ def converge_and_measure(GA, GB, lam, env, p, tol, max_sweeps, probe_sweeps=0):
     computations of the last sweep: how far (in decades) the multiplet decisions at the chi cut
     were from their thresholds when the readout was taken; ``c8_level`` is the largest s_K / s_1
     the multiplet rule moved out of the kept set there (0 when it moved nothing): a readout that
-    depends on keeping or dropping a multiplet of that size is one of several correct ones (C8).  With ``probe_sweeps`` > 0 a copy of the
-    converged environment is swept that many more times and ``drift`` records the largest change
-    of the one-site observables (occupations, imbalance, purity of rho_A): a converged readout that drifts away (a degenerate pair at the cut that
-    splits from rounding noise, C8) is not a unique result of the method.  The copy is first
-    perturbed by a seeded relative 1e-12, so that the probe does not depend on whether this
-    machine's rounding happens to break the symmetry."""
+    depends on keeping or dropping a multiplet of that size is one of several correct ones (C8).
+    ``ctm_stop`` says how the CTMRG ended: "tol" (delta < tol), "stall" (delta at its rounding
+    floor) or "cap" (max_sweeps reached).
+
+    With ``probe_sweeps`` > 0 the readout is probed for stability: a copy of the converged
+    environment is perturbed by a seeded relative 1e-6 and converged again by the same rules
+    (at most ``probe_sweeps`` sweeps); ``drift`` is the largest change of the one-site observables
+    (occupations, imbalance, purity of rho_A) between the two readouts.  At an attracting fixed
+    point the perturbation dies out and drift stays at the convergence level; at a fixed point
+    the CTMRG map departs from (an unstable one) or where several attractors lie close together,
+    the perturbed run ends elsewhere and drift is large: such a readout is not a unique result of
+    the method."""
     A, B, a = ctm_state(GA, GB, lam)
     if env is None:
         env = ctmrg.init_env(a, 2, 2, p['chi'], p['D'])
@@ -46,11 +52,10 @@ def converge_and_measure(GA, GB, lam, env, p, tol, max_sweeps, probe_sweeps=0):
                                      cut_rel=cut_rel, log=log)
     obs = measure.observables(A, B, env, p['J'], p['V'], p['h'], p.get('d_A', 2))
     last = log[-16:]
-    obs.update(ctm_sweeps=sweeps, ctm_delta=delta, c8_margin=float(min(m for m, _ in last)),
-               c8_level=float(max(v for _, v in last)))
+    stop = "tol" if delta < tol else ("cap" if sweeps >= max_sweeps else "stall")
+    obs.update(ctm_sweeps=sweeps, ctm_delta=delta, ctm_stop=stop,
+               c8_margin=float(min(m for m, _ in last)), c8_level=float(max(v for _, v in last)))
     if probe_sweeps > 0:
-        # seeded relative perturbation of 1e-12, so that an unstable fixed point (whose symmetric
-        # directions this machine's rounding may happen to preserve) shows up deterministically
         rng = np.random.default_rng(PROBE_SEED)
         e2 = env.copy()
         for group in (e2.C, e2.T):
@@ -59,16 +64,16 @@ def converge_and_measure(GA, GB, lam, env, p, tol, max_sweeps, probe_sweeps=0):
                     t = tens[key]
                     noise = rng.standard_normal(t.shape) + 1j * rng.standard_normal(t.shape)
                     tens[key] = t + PROBE_NOISE * np.abs(t).max() * noise
-        for _ in range(probe_sweeps):
-            e2 = ctmrg.sweep(a, e2, p['chi'], cut_rel)
+        e2, n2, d2 = ctmrg.ctmrg(a, e2, p['chi'], tol=tol, max_sweeps=probe_sweeps, cut_rel=cut_rel)
         before, after = _site_obs(A, B, env, p), _site_obs(A, B, e2, p)
         obs['drift'] = float(max(abs(after[k] - before[k]) for k in before))
+        obs['probe_sweeps'] = n2
     return env, obs
 
 
 def _site_obs(A, B, env, p):
     """The one-site part of the readout (occupations, imbalance, purity of rho_A), cheap enough to
-    evaluate after the probe sweeps."""
+    evaluate after the probe."""
     n = model.local_ops(p.get('d_A', 2))[1]
     rA, rB = measure.rho1(A, env, (0, 0)), measure.rho1(B, env, (1, 0))
     nA, nB = measure.expect1(rA, n).real, measure.expect1(rB, n).real

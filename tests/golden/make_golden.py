@@ -15,26 +15,36 @@ import os
 import sys
 import time
 
+import numpy as np
+
 HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 
 from inputs import QUENCH_D2, QUENCH_D3  # noqa: E402
 from oracle import evolve  # noqa: E402
 
-# sweeps run past every converged readout to see whether it stays put (evolve.converge_and_measure)
-PROBE = 25
+# at most this many sweeps for the stability probe of every readout (evolve.converge_and_measure)
+PROBE = 100
 
 KEYS = ("t", "nA", "nB", "imbalance", "tauzA", "tauzB", "energy", "purityA", "trunc_err_acc",
-        "ctm_sweeps", "ctm_delta", "c8_margin", "c8_level", "drift")
+        "ctm_sweeps", "ctm_delta", "ctm_stop", "c8_margin", "c8_level", "drift", "probe_sweeps")
+
+
+def _val(v):
+    if isinstance(v, str):
+        return v
+    if isinstance(v, (int, np.integer)):
+        return int(v)
+    return min(float(v), 99.0)          # c8_margin is inf when no multiplet decision was taken
 
 
 def _dump(path, params, out, seconds):
     rows = []
     for o in out:
-        r = {k: min(float(o[k]), 99.0) for k in KEYS}
+        r = {k: _val(o[k]) for k in KEYS}
         r["lam"] = [[float(x) for x in row] for row in o["lam"]]
         # the same readout converged from the traced start (gauge independent, see evolve.run)
-        r["cold"] = {k: min(float(o["cold"][k]), 99.0) for k in KEYS if k in o["cold"]}
+        r["cold"] = {k: _val(o["cold"][k]) for k in KEYS if k in o["cold"]}
         rows.append(r)
     with open(path, "w") as f:
         json.dump(dict(params=params, oracle_seconds=seconds, rows=rows), f, indent=1)
