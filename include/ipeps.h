@@ -115,6 +115,20 @@ ipeps_status ipeps_measure(ipeps_h h, ipeps_obs* out);
  * pos = x + 2 y of instance `inst`; sv_out: host double[chi]. */
 ipeps_status ipeps_corner_spectrum(ipeps_h h, int inst, int pos, int corner, double* sv_out);
 
+/* Copy out / replace the CTM environment of instance `inst` (Appendix: the corner and edge
+ * fixed-point tensors of CTMRG).  Host buffers, interleaved complex doubles:
+ *   C [4][4][chi][chi]       corners C1..C4 at unit-cell position pos = x + 2 y,
+ *                            C1[c_T4, c_T1], C2[c_T1, c_T2], C3[c_T2, c_T3], C4[c_T3, c_T4]
+ *   T [4][4][chi][D^2][chi]  edges T1..T4 at pos, T1[left, k, right], T2[up, k, down],
+ *                            T3[right, k, left], T4[down, k, up], k = ket * D + bra
+ * (each index joins the clockwise neighbour's: the last index of C1 is the first of T1, and so on).
+ * ipeps_get_env needs an environment (a previous ctmrg_converge or ipeps_set_env) and returns
+ * IPEPS_EINVAL otherwise.  ipeps_set_env makes the given tensors the environment of `inst` (the
+ * other instances keep theirs, or get the traced start when there was no environment yet); the
+ * next ctmrg_converge and ipeps_measure start from it.  Both synchronise the stream. */
+ipeps_status ipeps_get_env(ipeps_h h, int inst, double* C_out, double* T_out);
+ipeps_status ipeps_set_env(ipeps_h h, int inst, const double* C_in, const double* T_in);
+
 /* Copy out the bond weights (host double[batch][4][D]) / site tensors (host, layouts above). */
 ipeps_status ipeps_get_lambda(ipeps_h h, double* lambda_out);
 ipeps_status ipeps_get_tensors(ipeps_h h, double* gamma_A, double* gamma_B);

@@ -21,7 +21,10 @@ int ipeps_kernel_zgemm(int M, int N, int K, int batch, int opA, int opB,
                        const double* B, long long ldb, long long sB,
                        double* C, long long ldc, long long sC, void* stream);
 
-/* Allocation-free variant of ipeps_kernel_svd, same arguments and results.  The paper has no
+/* Allocation-free variant of ipeps_kernel_svd, same arguments and results for every block whose
+ * columns fit in the shared memory of one 8-CTA cluster (e.g. 162 x 26, 512 x 40, 256 x 256);
+ * taller blocks, which ipeps_kernel_svd serves through an allocated global-memory column buffer,
+ * are refused with IPEPS_EUNSUPPORTED.  The paper has no
  * counterpart: this exists for callers that cannot call cudaMalloc (an application allocator owns the
  * device memory, a plug-in only receives pre-allocated buffers, or device allocation is forbidden
  * after start-up).  Instead of allocating its operand pointer tables and error word per call, it
@@ -66,7 +69,7 @@ int ipeps_kernel_svd(int m, int n, int batch, const double* A, double* U, double
  * launch is then bracketed by CUDA events recorded on the stream it is launched on (this adds a
  * little host overhead); ipeps_profile_read synchronises the device and fills, per kernel class
  * (ipeps_profile_classes() entries, names from ipeps_profile_name), the summed event time in ms,
- * the summed algorithmic FP64 flops and the number of launches.  Arrays may be NULL. */
+ * the summed algorithmic flops and the number of launches.  Arrays may be NULL. */
 unsigned long long ipeps_launch_count(void);
 /* Measured FP64 FMA throughput of the current device in TFLOP/s (independent FMA chains on every
  * SM; best of three timed launches).  Allocates a small scratch buffer. */
@@ -75,6 +78,16 @@ int ipeps_profile_enable(int on);
 int ipeps_profile_classes(void);
 const char* ipeps_profile_name(int k);
 int ipeps_profile_read(double* ms, double* flops, unsigned long long* launches);
+/* Executed tensor-pipe flops (2 x rows x columns x depth of the real BF16 GEMMs, padding and the
+ * 3-term split included) of the tcgen05 GEMM launches since ipeps_profile_enable(1); the flops that
+ * ipeps_profile_read reports for that class are the complex products' algorithmic 8 M N K. */
+int ipeps_profile_tc_executed(double* flops_out);
+/* Device-side work counters since ipeps_profile_enable(1) (they count whether or not timing is on),
+ * out[0..n): Jacobi SVD problems factorised, their rotation rounds and sweeps (summed over
+ * problems), subspace-iteration rounds evaluated (summed over projector problems), projector
+ * problems whose subspace iteration met its acceptance test, and projector problems handed on at
+ * the round cap without meeting it.  Synchronises the device. */
+int ipeps_profile_counters(unsigned long long* out, int n);
 
 #ifdef __cplusplus
 }

@@ -4,7 +4,9 @@ The compute path is libipeps.so (hand-written CUDA for sm_103a behind a C ABI, i
 this package only loads it and marshals arguments.
 """
 from ._lib import (FP64, SPLIT_BF16X3, SPLIT_TF32X3, IPEPS, IpepsError, footprint_bytes, fp64_peak_tflops,
-                   launch_count, lib, profile_enable, profile_read)
+                   launch_count, lib, profile_enable, profile_read, profile_tc_executed,
+                   profile_counters)
 
 __all__ = ["FP64", "SPLIT_BF16X3", "SPLIT_TF32X3", "IPEPS", "IpepsError", "footprint_bytes",
-           "fp64_peak_tflops", "launch_count", "lib", "profile_enable", "profile_read"]
+           "fp64_peak_tflops", "launch_count", "lib", "profile_enable", "profile_read",
+           "profile_tc_executed", "profile_counters"]

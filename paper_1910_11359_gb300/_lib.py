@@ -46,7 +46,8 @@ EXPORTS = ["ipeps_init", "ipeps_set_tensors", "ipeps_trotter_step", "ctmrg_conve
            "ipeps_footprint_bytes", "ipeps_destroy", "ipeps_last_error", "ipeps_kernel_zgemm",
            "ipeps_kernel_permute", "ipeps_kernel_svd", "ipeps_kernel_gate", "ipeps_launch_count",
            "ipeps_profile_enable", "ipeps_profile_classes", "ipeps_profile_name", "ipeps_profile_read",
-           "ipeps_kernel_fp64_peak", "ipeps_kernel_svd_noalloc", "ipeps_kernel_zgemm_split"]
+           "ipeps_kernel_fp64_peak", "ipeps_kernel_svd_noalloc", "ipeps_kernel_zgemm_split",
+           "ipeps_get_env", "ipeps_set_env", "ipeps_profile_tc_executed", "ipeps_profile_counters"]
 
 
 def lib():
@@ -69,6 +70,8 @@ def lib():
     L.ipeps_corner_spectrum.argtypes = [vp, i, i, i, dp]
     L.ipeps_get_lambda.argtypes = [vp, dp]
     L.ipeps_get_tensors.argtypes = [vp, dp, dp]
+    L.ipeps_get_env.argtypes = [vp, i, dp, dp]
+    L.ipeps_set_env.argtypes = [vp, i, dp, dp]
     L.ipeps_footprint_bytes.argtypes = [P(Params), P(ctypes.c_size_t)]
     L.ipeps_destroy.argtypes = [vp]
     L.ipeps_last_error.argtypes = [vp]
@@ -84,6 +87,8 @@ def lib():
     L.ipeps_profile_name.argtypes = [i]
     L.ipeps_profile_name.restype = ctypes.c_char_p
     L.ipeps_profile_read.argtypes = [dp, dp, P(ctypes.c_ulonglong)]
+    L.ipeps_profile_tc_executed.argtypes = [dp]
+    L.ipeps_profile_counters.argtypes = [P(ctypes.c_ulonglong), i]
     L.ipeps_kernel_fp64_peak.argtypes = [dp]
     L.ipeps_kernel_svd_noalloc.argtypes = [i, i, i, vp, vp, vp, vp, d, i, vp, vp]
     L.ipeps_kernel_zgemm_split.argtypes = [i, i, i, i, i, i, vp, ll, ll, vp, ll, ll, vp, ll, ll, vp]
@@ -186,6 +191,22 @@ class IPEPS:
         _check(lib().ipeps_get_lambda(self._h, _dptr(out)), self._h)
         return out
 
+    def get_env(self, inst=0):
+        """(C, T) of instance ``inst``: C[i][pos] (chi x chi), T[i][pos] (chi x D^2 x chi),
+        i = 0..3 for C1..C4 / T1..T4, pos = x + 2 y."""
+        C = np.zeros((4, 4, self.chi, self.chi), dtype=np.complex128)
+        T = np.zeros((4, 4, self.chi, self.D * self.D, self.chi), dtype=np.complex128)
+        _check(lib().ipeps_get_env(self._h, inst, _dptr(C.view(np.float64)),
+                                   _dptr(T.view(np.float64))), self._h)
+        return C, T
+
+    def set_env(self, C, T, inst=0):
+        C = np.ascontiguousarray(C, dtype=np.complex128)
+        T = np.ascontiguousarray(T, dtype=np.complex128)
+        assert C.shape == (4, 4, self.chi, self.chi) and T.shape == (4, 4, self.chi, self.D ** 2, self.chi)
+        _check(lib().ipeps_set_env(self._h, inst, _dptr(C.view(np.float64)),
+                                   _dptr(T.view(np.float64))), self._h)
+
     def get_tensors(self):
         shape = (self.batch, self.d) + (self.D,) * 4
         GA = np.zeros(shape, dtype=np.complex128)
@@ -212,6 +233,24 @@ def profile_read():
     cnt = np.zeros(n, dtype=np.uint64)
     _check(L.ipeps_profile_read(_dptr(ms), _dptr(fl), cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_ulonglong))))
     return {L.ipeps_profile_name(k).decode(): (float(ms[k]), float(fl[k]), int(cnt[k])) for k in range(n)}
+
+
+def profile_tc_executed():
+    """Executed tensor-pipe flops of the tcgen05 GEMM launches since profile_enable(True)."""
+    out = ctypes.c_double(0.0)
+    _check(lib().ipeps_profile_tc_executed(ctypes.byref(out)))
+    return out.value
+
+
+COUNTERS = ("jacobi_problems", "jacobi_rounds", "jacobi_sweeps", "subspace_rounds",
+            "subspace_accepted", "subspace_unconverged")
+
+
+def profile_counters():
+    """Device-side work counters since profile_enable(True), as a dict (see COUNTERS)."""
+    out = np.zeros(len(COUNTERS), dtype=np.uint64)
+    _check(lib().ipeps_profile_counters(out.ctypes.data_as(ctypes.POINTER(ctypes.c_ulonglong)), len(COUNTERS)))
+    return {k: int(v) for k, v in zip(COUNTERS, out)}
 
 
 def fp64_peak_tflops():

@@ -388,6 +388,48 @@ ipeps_status ipeps_corner_spectrum(ipeps_h h, int inst, int pos, int corner, dou
   return IPEPS_OK;
 }
 
+ipeps_status ipeps_get_env(ipeps_h h, int inst, double* C_out, double* T_out) {
+  if (!h || !C_out || !T_out) return fail(h, IPEPS_EINVAL, "NULL argument");
+  Ctx& c = h->c;
+  if (inst < 0 || inst >= c.B) return fail(h, IPEPS_EINVAL, "instance out of range");
+  if (!c.env_valid) return fail(h, IPEPS_EINVAL, "no environment: call ctmrg_converge first");
+  const size_t nC = (size_t)c.chi * c.chi, nT = (size_t)c.chi * c.D2 * c.chi;
+  for (int i = 0; i < 4; ++i)
+    for (int p = 0; p < NPOS; ++p) {
+      cplx* dC = (cplx*)C_out + (size_t)(i * NPOS + p) * nC;
+      cplx* dT = (cplx*)T_out + (size_t)(i * NPOS + p) * nT;
+      if (cudaMemcpyAsync(dC, c.Cenv[i][p] + (size_t)inst * nC, nC * sizeof(cplx), cudaMemcpyDeviceToHost,
+                          c.st) != cudaSuccess ||
+          cudaMemcpyAsync(dT, c.Tenv[i][p] + (size_t)inst * nT, nT * sizeof(cplx), cudaMemcpyDeviceToHost,
+                          c.st) != cudaSuccess)
+        return from_rc(h, cuda_fail(cudaGetLastError(), "get_env", __FILE__, __LINE__));
+    }
+  return check_dev(h);
+}
+
+ipeps_status ipeps_set_env(ipeps_h h, int inst, const double* C_in, const double* T_in) {
+  if (!h || !C_in || !T_in) return fail(h, IPEPS_EINVAL, "NULL argument");
+  Ctx& c = h->c;
+  if (inst < 0 || inst >= c.B) return fail(h, IPEPS_EINVAL, "instance out of range");
+  int rc;
+  if (!c.env_valid) {
+    // the other instances get the traced start of their current tensors
+    if ((rc = ctm_prepare_tensors(c)) || (rc = ctm_init_env(c))) return from_rc(h, rc);
+  }
+  const size_t nC = (size_t)c.chi * c.chi, nT = (size_t)c.chi * c.D2 * c.chi;
+  for (int i = 0; i < 4; ++i)
+    for (int p = 0; p < NPOS; ++p) {
+      const cplx* sC = (const cplx*)C_in + (size_t)(i * NPOS + p) * nC;
+      const cplx* sT = (const cplx*)T_in + (size_t)(i * NPOS + p) * nT;
+      if (cudaMemcpyAsync(c.Cenv[i][p] + (size_t)inst * nC, sC, nC * sizeof(cplx), cudaMemcpyHostToDevice,
+                          c.st) != cudaSuccess ||
+          cudaMemcpyAsync(c.Tenv[i][p] + (size_t)inst * nT, sT, nT * sizeof(cplx), cudaMemcpyHostToDevice,
+                          c.st) != cudaSuccess)
+        return from_rc(h, cuda_fail(cudaGetLastError(), "set_env", __FILE__, __LINE__));
+    }
+  return check_dev(h);
+}
+
 ipeps_status ipeps_get_lambda(ipeps_h h, double* lambda_out) {
   if (!h || !lambda_out) return fail(h, IPEPS_EINVAL, "NULL argument");
   Ctx& c = h->c;

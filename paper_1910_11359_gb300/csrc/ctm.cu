@@ -317,7 +317,8 @@ constexpr double kDegenRtol = 1e-10, kDegenAbs = 1e-11, kTinyRel = 1e-14;
 __global__ void proj_prep_kernel(const double* S, long long s_stride, int ns, const cplx* U,
                                  const cplx* V, int N, int chi, long long ldu, long long stride_uv,
                                  cplx* Us, cplx* Vs, int* kept, double degen_rtol, double degen_abs,
-                                 double tiny_rel, double cut_rel) {
+                                 double tiny_rel, double cut_rel, const int* done = nullptr,
+                                 unsigned long long* ctr = nullptr) {
   // S: ns singular values (descending) per problem; U, V: N x (>= chi) with leading dimension ldu
   const int q = blockIdx.x;
   const double* s = S + (size_t)q * s_stride;
@@ -334,6 +335,7 @@ __global__ void proj_prep_kernel(const double* S, long long s_stride, int ns, co
     else if (K < 1) K = 1;
     sK = K;
     kept[q] = K;
+    if (done && ctr && !done[q]) atomicAdd(ctr + CTR_SUB_UNCONVERGED, 1ull);
   }
   __syncthreads();
   const int K = sK;
@@ -443,12 +445,14 @@ __global__ void normalize_store_kernel(const cplx* C1n, const cplx* T4n, const c
 // Convergence number per instance: max over the 16 corners of || s/s_1 - s_prev/s_1,prev ||_2.
 // first != 0 only records the spectra of the starting environment.  An instance is frozen (its
 // environment no longer updated) once delta < tol, or once delta has stalled at its rounding floor:
-// no factor-2 improvement of the best delta for kStallWindow sweeps while that best is below
-// stall_max ("sufficiently well converged", Appendix): kStallMax on the FP64 path,
-// kStallMaxSplit on the split path, whose contractions leave a noise floor near 1e-6.
-// tol <= 0 never freezes.
+// no factor-2 improvement of the best delta for kStallWindow sweeps while that best and the current
+// delta are below stall_max and the current delta is within kStallGrowth of the best
+// ("sufficiently well converged", Appendix): kStallMax on the FP64 path, kStallMaxSplit on the
+// split path, whose contractions leave a noise floor near 1e-6.  A delta that grows again after
+// coming close to a fixed point means the environment is leaving an unstable fixed point; the
+// instance keeps sweeping.  tol <= 0 never freezes.
 constexpr int kStallWindow = 10;
-constexpr double kStallMax = 1e-7, kStallMaxSplit = 1e-5;
+constexpr double kStallMax = 1e-7, kStallMaxSplit = 1e-5, kStallGrowth = 4.0;
 
 __global__ void spectra_delta_kernel(const double* cs, double* prev, int B, int chi, int first,
                                      double tol, double stall_max, double* delta, int* frozen, int* sweeps,
@@ -492,7 +496,9 @@ __global__ void spectra_delta_kernel(const double* cs, double* prev, int B, int 
   } else {
     since[b] += 1;
   }
-  if (tol > 0.0 && since[b] >= kStallWindow && best[b] < stall_max) frozen[b] = 1;
+  if (tol > 0.0 && since[b] >= kStallWindow && best[b] < stall_max && m < stall_max &&
+      m <= kStallGrowth * best[b])
+    frozen[b] = 1;
 }
 
 // ----------------------------------------------------------------------------- drivers
@@ -570,7 +576,7 @@ __global__ void sub_refill_kernel(cplx* Z, int N, int k, unsigned long long seed
 // residual_j = || (M^+ U_y)_j - s_j (V_f)_j || <= rtol * s_1 for the first min(k, chi + 1) columns.
 __global__ void sub_residual_kernel(const cplx* Z, const cplx* Vf, const double* S, int N, int k,
                                     int ncheck, double rtol, double stag, int* done, int* rounds,
-                                    double* prev) {
+                                    double* prev, unsigned long long* ctr) {
   const int q = blockIdx.x;
   if (done[q]) return;
   const cplx* Zq = Z + (size_t)q * N * k;
@@ -597,9 +603,13 @@ __global__ void sub_residual_kernel(const cplx* Z, const cplx* Vf, const double*
     const double r = sqrt(worst);
     // accepted at rtol, or once the residual stops shrinking (factor 2 per round) below stag s_1:
     // then it sits at the rounding floor of the small directions
-    if (r <= rtol * s[0] || (rounds[q] > 0 && r <= stag * s[0] && r > 0.5 * prev[q])) done[q] = 1;
+    if (r <= rtol * s[0] || (rounds[q] > 0 && r <= stag * s[0] && r > 0.5 * prev[q])) {
+      done[q] = 1;
+      if (ctr) atomicAdd(ctr + CTR_SUB_ACCEPTED, 1ull);
+    }
     prev[q] = r;
     rounds[q] += 1;
+    if (ctr) atomicAdd(ctr + CTR_SUB_ROUNDS, 1ull);
   }
 }
 
@@ -651,7 +661,8 @@ static int subspace_svd(Ctx& c, int f, int x, const cplx* R, const cplx* Rt) {
     if ((rc = zgemm_f64(g, st))) return rc;
     IPEPS_LAUNCH(K_PROJ_PREP, 0, st,
                  sub_residual_kernel<<<2 * B, 256, 0, st>>>(w.Zsub, slot, w.Sy, N, k, ncheck, rtol,
-                                                            stag, w.sub_done, w.sub_rounds, w.sub_res));
+                                                            stag, w.sub_done, w.sub_rounds, w.sub_res,
+                                                            prof_device_counters()));
     if (it + 1 == rounds) break;
     IPEPS_LAUNCH(K_PROJ_PREP, 0, st,
                  sub_refill_kernel<<<2 * B, 256, 0, st>>>(w.Zsub, N, k, c.seed, stream_id * 1000 + it,
@@ -664,7 +675,8 @@ static int subspace_svd(Ctx& c, int f, int x, const cplx* R, const cplx* Rt) {
   c.slot_warm[f][x] = true;
   IPEPS_LAUNCH(K_PROJ_PREP, 0, st,
                proj_prep_kernel<<<2 * B, 256, 2 * chi * sizeof(double), st>>>(w.Sy, k, k, w.Uy, slot, N, chi, k, Nk, w.Us,
-                                                       w.Vs, w.kept, kDegenRtol, kDegenAbs, kTinyRel, c.cut_rel));
+                                                       w.Vs, w.kept, kDegenRtol, kDegenAbs, kTinyRel, c.cut_rel,
+                                                       w.sub_done, prof_device_counters()));
   return 0;
 }
 

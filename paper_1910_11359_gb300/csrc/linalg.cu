@@ -2,6 +2,7 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "linalg.cuh"
 #include "prof.cuh"
@@ -130,6 +131,7 @@ struct JacobiArgs {
   int np, ra, rw;
   int lpp;                     // lanes per pair in the dot-product phase (power of two, 4..32)
   unsigned long long* flops;   // algorithmic flop counter (dot products + applied rotations)
+  unsigned long long* ctr;     // work counters (problems, rounds, sweeps)
 };
 
 // Round-robin ("circle") tournament: position 0 fixed, the rest rotate by one each round, so every
@@ -383,6 +385,11 @@ __global__ void __launch_bounds__(JTHREADS) jacobi_kernel(JacobiArgs args) {
       const double work = 16.0 * m * npairs * (double)gcount + 14.0 * (m + n) * (double)nrot_total;
       atomicAdd(args.flops, (unsigned long long)work);
     }
+    if (args.ctr) {
+      atomicAdd(args.ctr + CTR_JACOBI_PROBLEMS, 1ull);
+      atomicAdd(args.ctr + CTR_JACOBI_ROUNDS, (unsigned long long)gcount);
+      atomicAdd(args.ctr + CTR_JACOBI_SWEEPS, (unsigned long long)(sweep + 1));
+    }
     if (d.sweeps_out) d.sweeps_out[prob] = sweep + 1;
     if (d.err) {
       if (nonfinite_any) atomicOr(d.err, (unsigned)DEV_NONFINITE);
@@ -437,10 +444,11 @@ size_t jacobi_svd_global_bytes(int m, int n, int batch) {
 }
 
 // 16-CTA clusters are a non-portable size: used when the device accepts them for this kernel
+// (probed once per process; the library drives one device per process)
 static bool tall_clusters_available() {
-  static int state = -1;
-  if (state < 0) {
-    state = 0;
+  static std::once_flag once;
+  static int state = 0;
+  std::call_once(once, [] {
     if (cudaFuncSetAttribute(jacobi_kernel<JCS_TALL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
             cudaSuccess &&
         cudaFuncSetAttribute(jacobi_kernel<JCS_TALL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -462,18 +470,19 @@ static bool tall_clusters_available() {
         state = 1;
     }
     cudaGetLastError();
-  }
+  });
   return state == 1;
 }
 
 template <int CS>
 static int launch_jacobi(const JacobiArgs& a, size_t smem, int batch, cudaStream_t st) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    IPEPS_CUDA_TRY(cudaFuncSetAttribute(jacobi_kernel<CS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        200 * 1024 + 1024));
-    attr_set = true;
-  }
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [] {
+    attr_err = cudaFuncSetAttribute(jacobi_kernel<CS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    200 * 1024 + 1024);
+  });
+  IPEPS_CUDA_TRY(attr_err);
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -506,6 +515,7 @@ int jacobi_svd(const SvdDesc& d, cudaStream_t st) {
   jacobi_layout(d.m, d.n, cs, &a.np, &a.ra, &a.rw);
   const size_t smem = in_smem ? smem_bytes_cs(d.m, d.n, cs) : small_smem_bytes_cs(d.m, d.n, cs);
   a.flops = prof_device_flops();
+  a.ctr = prof_device_counters();
   // dot-product lanes per pair: about 4 rows per lane, 4..32 lanes
   a.lpp = 4;
   while (a.lpp < 32 && a.lpp * 4 < a.ra) a.lpp *= 2;

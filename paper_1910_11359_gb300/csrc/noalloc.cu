@@ -83,7 +83,8 @@ extern "C" int ipeps_kernel_svd_noalloc(int m, int n, int batch, const double* A
     return IPEPS_EINVAL;
   }
   if (!jacobi_svd_fits(m, n)) {
-    set_thread_error("svd size too large");
+    set_thread_error("ipeps_kernel_svd_noalloc: the m x n block does not fit in the shared memory of "
+                     "one cluster (ipeps_kernel_svd serves such blocks with an allocated column buffer)");
     return IPEPS_EUNSUPPORTED;
   }
   unsigned char* scratch = nullptr;

@@ -17,15 +17,15 @@ const char* kNames[K_NCLASS] = {"zgemm_f64", "permute", "jacobi_svd", "su_absorb
                                 "tc_gemm_bf16", "tc_split_prep"};
 std::atomic<unsigned long long> g_launches{0};
 std::mutex g_mu;
-bool g_on = false;
+std::atomic<bool> g_on{false};
 struct Rec { int cls; cudaEvent_t a, b; double flops; };
 std::vector<Rec> g_recs;
 std::vector<cudaEvent_t> g_free;
-cudaEvent_t g_pending_start[K_NCLASS];
 double g_flops[K_NCLASS];
 unsigned long long g_count[K_NCLASS];
 double g_ms[K_NCLASS];
 unsigned long long g_devflops_host[K_NCLASS];
+double g_tc_executed = 0.0;
 
 cudaEvent_t take_event() {
   if (!g_free.empty()) {
@@ -40,30 +40,66 @@ cudaEvent_t take_event() {
 }  // namespace
 
 __device__ unsigned long long g_dev_flops;
+__device__ unsigned long long g_dev_ctr[CTR_N];
 
-unsigned long long* prof_device_flops() {
-  unsigned long long* p = nullptr;
-  cudaGetSymbolAddress((void**)&p, g_dev_flops);
-  return p;
+namespace {
+// device addresses of the counters, looked up once per device
+constexpr int kMaxDev = 64;
+std::mutex g_sym_mu;
+unsigned long long* g_flops_addr[kMaxDev] = {nullptr};
+unsigned long long* g_ctr_addr[kMaxDev] = {nullptr};
+
+unsigned long long* symbol_addr(unsigned long long** cache, const void* sym) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return nullptr;
+  std::lock_guard<std::mutex> lk(g_sym_mu);
+  if (!cache[dev]) {
+    unsigned long long* p = nullptr;
+    if (cudaGetSymbolAddress((void**)&p, sym) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    cache[dev] = p;
+  }
+  return cache[dev];
 }
+}  // namespace
+
+unsigned long long* prof_device_flops() { return symbol_addr(g_flops_addr, (const void*)&g_dev_flops); }
+
+unsigned long long* prof_device_counters() { return symbol_addr(g_ctr_addr, (const void*)&g_dev_ctr); }
 
 const char* kernel_class_name(int k) { return (k >= 0 && k < K_NCLASS) ? kNames[k] : "?"; }
 
-void prof_begin(int cls, cudaStream_t st) {
-  g_launches.fetch_add(1, std::memory_order_relaxed);
-  if (!g_on) return;
+void prof_add_tc_executed(double flops) {
+  if (!g_on.load(std::memory_order_relaxed)) return;
   std::lock_guard<std::mutex> lk(g_mu);
-  cudaEvent_t e = take_event();
-  cudaEventRecord(e, st);
-  g_pending_start[cls] = e;
+  g_tc_executed += flops;
 }
 
-void prof_end(int cls, cudaStream_t st, double flops) {
-  if (!g_on) return;
-  std::lock_guard<std::mutex> lk(g_mu);
-  cudaEvent_t e = take_event();
+cudaEvent_t prof_begin(int cls, cudaStream_t st) {
+  (void)cls;
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  if (!g_on.load(std::memory_order_relaxed)) return nullptr;
+  cudaEvent_t e;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    e = take_event();
+  }
   cudaEventRecord(e, st);
-  g_recs.push_back({cls, g_pending_start[cls], e, flops});
+  return e;
+}
+
+void prof_end(int cls, cudaStream_t st, double flops, cudaEvent_t start) {
+  if (!start) return;
+  cudaEvent_t e;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    e = take_event();
+  }
+  cudaEventRecord(e, st);
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_recs.push_back({cls, start, e, flops});
 }
 
 }  // namespace ipeps
@@ -80,13 +116,31 @@ int ipeps_profile_enable(int on) {
   for (auto& r : g_recs) { g_free.push_back(r.a); g_free.push_back(r.b); }
   g_recs.clear();
   for (int k = 0; k < K_NCLASS; ++k) { g_flops[k] = 0; g_count[k] = 0; g_ms[k] = 0; }
-  unsigned long long zero = 0;
-  cudaMemcpyToSymbol(g_dev_flops, &zero, sizeof(zero));
-  g_on = on != 0;
+  g_tc_executed = 0.0;
+  unsigned long long zero[CTR_N] = {0};
+  cudaMemcpyToSymbol(g_dev_flops, zero, sizeof(unsigned long long));
+  cudaMemcpyToSymbol(g_dev_ctr, zero, sizeof(zero));
+  g_on.store(on != 0);
   return 0;
 }
 
 int ipeps_profile_classes(void) { return K_NCLASS; }
+
+int ipeps_profile_counters(unsigned long long* out, int n) {
+  if (!out || n < 1) return 1;
+  unsigned long long v[CTR_N] = {0};
+  if (cudaDeviceSynchronize() != cudaSuccess) return 5;
+  cudaMemcpyFromSymbol(v, g_dev_ctr, sizeof(v));
+  for (int i = 0; i < n; ++i) out[i] = i < CTR_N ? v[i] : 0;
+  return 0;
+}
+
+int ipeps_profile_tc_executed(double* flops_out) {
+  if (!flops_out) return 1;
+  std::lock_guard<std::mutex> lk(g_mu);
+  *flops_out = g_tc_executed;
+  return 0;
+}
 
 const char* ipeps_profile_name(int k) { return kernel_class_name(k); }
 

@@ -13,16 +13,32 @@ enum KernelClass : int {
 };
 
 const char* kernel_class_name(int k);
-void prof_begin(int cls, cudaStream_t st);
-void prof_end(int cls, cudaStream_t st, double flops);
+// prof_begin counts the launch and, while timing is on, records and returns its start event
+// (nullptr otherwise); prof_end records the matching end event.  The start event travels with the
+// launch site, so launches of one class from several host threads pair their own events.
+cudaEvent_t prof_begin(int cls, cudaStream_t st);
+void prof_end(int cls, cudaStream_t st, double flops, cudaEvent_t start);
 // device-side flop counter used by kernels whose work is data dependent (Jacobi sweeps)
 unsigned long long* prof_device_flops();
+// device-side work counters (reset by ipeps_profile_enable): indices below
+enum DevCounter : int {
+  CTR_JACOBI_PROBLEMS = 0,   // Jacobi SVD problems factorised (skipped ones not counted)
+  CTR_JACOBI_ROUNDS,         // rotation rounds run, summed over problems
+  CTR_JACOBI_SWEEPS,         // sweeps run, summed over problems
+  CTR_SUB_ROUNDS,            // subspace-iteration rounds evaluated, summed over projector problems
+  CTR_SUB_ACCEPTED,          // projector problems whose subspace iteration met its acceptance test
+  CTR_SUB_UNCONVERGED,       // projector problems handed on at the round cap without meeting it
+  CTR_N
+};
+unsigned long long* prof_device_counters();
+// executed tensor-pipe flops of the tcgen05 GEMM launches (tallied while timing is on)
+void prof_add_tc_executed(double flops);
 
 }  // namespace ipeps
 
-#define IPEPS_LAUNCH(cls, flops, st, ...)             \
-  do {                                               \
-    ::ipeps::prof_begin((cls), (st));                \
-    __VA_ARGS__;                                     \
-    ::ipeps::prof_end((cls), (st), (double)(flops)); \
+#define IPEPS_LAUNCH(cls, flops, st, ...)                                  \
+  do {                                                                    \
+    cudaEvent_t ipeps_launch_start_ = ::ipeps::prof_begin((cls), (st));  \
+    __VA_ARGS__;                                                          \
+    ::ipeps::prof_end((cls), (st), (double)(flops), ipeps_launch_start_); \
   } while (0)

@@ -393,17 +393,19 @@ size_t split_workspace_bytes(int M, int N, int K, int batch) {
 
 template <int BN>
 static int launch_tc(const CUtensorMap& mA, const CUtensorMap& mB, float* C32, int Mp, int Np, int Kp,
-                     int batch, unsigned* err, cudaStream_t st) {
+                     int batch, double algo_flops, unsigned* err, cudaStream_t st) {
   using Cfg = TileCfg<BN>;
-  static bool attr = false;
-  if (!attr) {
-    IPEPS_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)Cfg::SMEM_BYTES));
-    attr = true;
-  }
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [] {
+    attr_err = cudaFuncSetAttribute(tc_gemm_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)Cfg::SMEM_BYTES);
+  });
+  IPEPS_CUDA_TRY(attr_err);
   dim3 grid(Np / BN, Mp / BM, batch);
-  const double flops = 2.0 * Mp * (double)Np * Kp * batch;
-  IPEPS_LAUNCH(K_TC_GEMM, flops, st,
+  const double flops = 2.0 * Mp * (double)Np * Kp * batch;     // executed on the tensor pipe
+  prof_add_tc_executed(flops);
+  IPEPS_LAUNCH(K_TC_GEMM, algo_flops > 0.0 ? algo_flops : flops, st,
                tc_gemm_kernel<BN><<<grid, THREADS, Cfg::SMEM_BYTES, st>>>(mA, mB, C32, Np, (long long)Mp * Np,
                                                                         Kp / BK, err));
   IPEPS_CUDA_TRY(cudaGetLastError());
@@ -411,7 +413,7 @@ static int launch_tc(const CUtensorMap& mA, const CUtensorMap& mB, float* C32, i
 }
 
 int gemm_bf16_raw(const void* A3, const void* B3t, float* C32, int Mp, int Np, int Kp, int batch,
-                  int bn, unsigned* err, cudaStream_t st) {
+                  int bn, double algo_flops, unsigned* err, cudaStream_t st) {
   if ((bn != 128 && bn != 256) || Mp % BM || Np % bn || Kp % BK || batch < 1 || batch > 65535)
     return cuda_fail(cudaErrorInvalidValue, "tc gemm shape", __FILE__, __LINE__);
   if (((uintptr_t)A3 & 15) || ((uintptr_t)B3t & 15) || ((uintptr_t)C32 & 15))
@@ -419,8 +421,8 @@ int gemm_bf16_raw(const void* A3, const void* B3t, float* C32, int Mp, int Np, i
   CUtensorMap mA, mB;
   if (int rc = make_map(&mA, A3, Mp, Kp, batch, BM)) return rc;
   if (int rc = make_map(&mB, B3t, Np, Kp, batch, bn)) return rc;
-  return bn == 256 ? launch_tc<256>(mA, mB, C32, Mp, Np, Kp, batch, err, st)
-                   : launch_tc<128>(mA, mB, C32, Mp, Np, Kp, batch, err, st);
+  return bn == 256 ? launch_tc<256>(mA, mB, C32, Mp, Np, Kp, batch, algo_flops, err, st)
+                   : launch_tc<128>(mA, mB, C32, Mp, Np, Kp, batch, algo_flops, err, st);
 }
 
 int zgemm_split_bf16(const GemmDesc& g, void* work, size_t work_bytes, unsigned* err, cudaStream_t st) {
@@ -448,7 +450,8 @@ int zgemm_split_bf16(const GemmDesc& g, void* work, size_t work_bytes, unsigned*
   IPEPS_LAUNCH(K_TC_PREP, 0, st, prep_a_kernel<<<pa, pblk, 0, st>>>(g, A3, Mp, Kp));
   IPEPS_LAUNCH(K_TC_PREP, 0, st, prep_b_kernel<<<pb, pblk, 0, st>>>(g, B3, Np, Kp));
   IPEPS_CUDA_TRY(cudaGetLastError());
-  if (int rc = gemm_bf16_raw(A3, B3, C32, Mp, Np, Kp, g.batch, bn, err, st)) return rc;
+  const double algo = 8.0 * g.M * (double)g.N * g.K * g.batch;   // the complex product's own flops
+  if (int rc = gemm_bf16_raw(A3, B3, C32, Mp, Np, Kp, g.batch, bn, algo, err, st)) return rc;
   const dim3 gc((g.N + 255) / 256, g.M, g.batch);
   IPEPS_LAUNCH(K_TC_PREP, 0, st, gather_c_kernel<<<gc, 256, 0, st>>>(g, C32, Mp, Np));
   IPEPS_CUDA_TRY(cudaGetLastError());
