@@ -26,7 +26,7 @@ __device__ __forceinline__ cplx load_op(const cplx* P, long long ld, int op, int
 
 __global__ void __launch_bounds__(GT * GT) zgemm_kernel(GemmDesc g) {
   const int b = blockIdx.z;
-  if (g.skip && g.skip[b]) return;
+  if (skipped(g.skip, g.skip_mod, b)) return;
   const cplx* A = g.Aptr ? g.Aptr[b] : g.A + (long long)b * g.sA;
   const cplx* B = g.Bptr ? g.Bptr[b] : g.B + (long long)b * g.sB;
   cplx* C = g.Cptr ? g.Cptr[b] : g.C + (long long)b * g.sC;
@@ -80,11 +80,13 @@ struct PermArgs {
 };
 
 __global__ void permute_kernel(const cplx* __restrict__ in, cplx* __restrict__ out, PermArgs a,
-                               long long total, int batch, long long s_in, long long s_out) {
+                               long long total, int batch, long long s_in, long long s_out,
+                               const int* skip, int skip_mod) {
   long long n = total * batch;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
        idx += (long long)gridDim.x * blockDim.x) {
     long long b = idx / total, o = idx - b * total;
+    if (skipped(skip, skip_mod, (int)b)) continue;
     long long rem = o, off = 0;
     for (int j = a.rank - 1; j >= 0; --j) {
       long long c = rem % a.out_dims[j];
@@ -96,7 +98,7 @@ __global__ void permute_kernel(const cplx* __restrict__ in, cplx* __restrict__ o
 }
 
 int permute_c128(const cplx* in, cplx* out, int rank, const int* dims, const int* perm, int batch,
-                 long long s_in, long long s_out, cudaStream_t st) {
+                 long long s_in, long long s_out, cudaStream_t st, const int* skip, int skip_mod) {
   if (rank < 1 || rank > 8) return cuda_fail(cudaErrorInvalidValue, "permute rank", __FILE__, __LINE__);
   PermArgs a;
   a.rank = rank;
@@ -113,7 +115,8 @@ int permute_c128(const cplx* in, cplx* out, int rank, const int* dims, const int
   int threads = 256;
   long long blocks = std::min<long long>((n + threads - 1) / threads, 152LL * 16);
   IPEPS_LAUNCH(K_PERMUTE, 0, st,
-               permute_kernel<<<(unsigned)blocks, threads, 0, st>>>(in, out, a, total, batch, s_in, s_out));
+               permute_kernel<<<(unsigned)blocks, threads, 0, st>>>(in, out, a, total, batch, s_in, s_out,
+                                                                    skip, skip_mod));
   IPEPS_CUDA_TRY(cudaGetLastError());
   return 0;
 }
@@ -203,7 +206,7 @@ __global__ void __launch_bounds__(JTHREADS) jacobi_kernel(JacobiArgs args) {
   const int m = d.m, n = d.n;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = JTHREADS / 32;
   // skipped problems: every CTA of the cluster reads the same flag and leaves before any barrier
-  if (d.skip && d.skip[prob]) return;
+  if (skipped(d.skip, d.skip_mod, prob)) return;
 
   extern __shared__ __align__(16) unsigned char jsm_raw[];
   // the CTA's row slices of the columns: in shared memory, or in its own region of d.gwork
@@ -354,9 +357,15 @@ __global__ void __launch_bounds__(JTHREADS) jacobi_kernel(JacobiArgs args) {
     sig[j] = sqrt(s);
   }
   __syncthreads();
+  // rank by a key that orders NaN below every norm, so that the ranks form a permutation of
+  // [0, n) whatever the data (a NaN compares false both ways and would leave ranks unassigned)
   for (int j = tid; j < n; j += JTHREADS) {
+    const double kj = sig[j] == sig[j] ? sig[j] : -1.0;
     int rk = 0;
-    for (int k = 0; k < n; ++k) rk += (sig[k] > sig[j]) || (sig[k] == sig[j] && k < j);
+    for (int k = 0; k < n; ++k) {
+      const double kk = sig[k] == sig[k] ? sig[k] : -1.0;
+      rk += (kk > kj) || (kk == kj && k < j);
+    }
     order[rk] = j;
   }
   __syncthreads();

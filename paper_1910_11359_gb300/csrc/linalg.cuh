@@ -19,14 +19,21 @@ struct GemmDesc {
   const cplx* A; const cplx* B; cplx* C;
   const cplx* const* Aptr; const cplx* const* Bptr; cplx* const* Cptr;
   cplx alpha, beta;
-  const int* skip;                // optional [batch]: problems with skip[b] != 0 are left untouched
+  const int* skip;                // optional: problem b is left untouched when skip[b] != 0, or
+  int skip_mod;                   // skip[b % skip_mod] != 0 when skip_mod > 0 (per-instance flags)
 };
+
+__host__ __device__ __forceinline__ bool skipped(const int* skip, int skip_mod, int b) {
+  return skip && skip[skip_mod > 0 ? b % skip_mod : b];
+}
 
 int zgemm_f64(const GemmDesc& g, cudaStream_t st);
 
-// out = permute(in): out axis j is in axis perm[j]; rank <= 8; batched with element strides.
+// out = permute(in): out axis j is in axis perm[j]; rank <= 8; batched with element strides;
+// problems with skipped(skip, skip_mod, b) are left untouched.
 int permute_c128(const cplx* in, cplx* out, int rank, const int* dims, const int* perm, int batch,
-                 long long s_in, long long s_out, cudaStream_t st);
+                 long long s_in, long long s_out, cudaStream_t st, const int* skip = nullptr,
+                 int skip_mod = 0);
 
 // One-sided (Hestenes) Jacobi SVD of a batch of m x n complex matrices (m >= n), A = U S V^+.
 // Each problem is handled by one thread-block cluster (8 CTAs, or 16 for m >= 1024 where the part
@@ -44,7 +51,8 @@ struct SvdDesc {
   int max_sweeps;
   unsigned* err;       // device error word (DevErr bits)
   int* sweeps_out;     // optional: sweeps used per problem (1 = the input columns were orthogonal)
-  const int* skip;     // optional [batch]: problems with skip[b] != 0 are left untouched
+  const int* skip;     // optional: problems with skipped(skip, skip_mod, b) are left untouched
+  int skip_mod = 0;
   // optional global-memory column storage for blocks whose rows do not fit in shared memory
   // (jacobi_svd_global_bytes(m, n, batch) bytes; the columns then live in L2 instead of SMEM)
   cplx* gwork = nullptr;

@@ -92,7 +92,10 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
 template <int BN>
 __global__ void __launch_bounds__(THREADS, 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-               float* __restrict__ C, long long ldc, long long strideC, int ktiles, unsigned* err) {
+               float* __restrict__ C, long long ldc, long long strideC, int ktiles, unsigned* err,
+               const int* skip, int skip_mod) {
+  // skipped problems: the whole CTA leaves before any barrier, TMA load or TMEM allocation
+  if (skipped(skip, skip_mod, (int)blockIdx.z)) return;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   unsigned char* smem = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
@@ -277,6 +280,7 @@ __device__ __forceinline__ void load_tile(cplx (*tile)[PT + 1], const cplx* P, l
 __global__ void __launch_bounds__(256) prep_a_kernel(GemmDesc g, __nv_bfloat16* A3, int Mp, int Kp) {
   __shared__ cplx tile[PT][PT + 1];
   const int b = blockIdx.z, M = g.M, K = g.K;
+  if (skipped(g.skip, g.skip_mod, b)) return;
   const int row0 = blockIdx.y * PT, k0 = blockIdx.x * PT;
   const cplx* A = g.Aptr ? g.Aptr[b] : g.A + (long long)b * g.sA;
   // op(A)[r][k]: OP_N reads A[r * lda + k]; OP_T and OP_C read A[k * lda + r]
@@ -307,6 +311,7 @@ __global__ void __launch_bounds__(256) prep_a_kernel(GemmDesc g, __nv_bfloat16* 
 __global__ void __launch_bounds__(256) prep_b_kernel(GemmDesc g, __nv_bfloat16* B3t, int Np, int Kp) {
   __shared__ cplx tile[PT][PT + 1];
   const int b = blockIdx.z, N = g.N, K = g.K;
+  if (skipped(g.skip, g.skip_mod, b)) return;
   const int row0 = blockIdx.y * PT, k0 = blockIdx.x * PT;
   const cplx* B = g.Bptr ? g.Bptr[b] : g.B + (long long)b * g.sB;
   // op(B)^T[j][k] = op(B)[k][j]: OP_N reads B[k * ldb + j]; OP_T and OP_C read B[j * ldb + k]
@@ -331,6 +336,7 @@ __global__ void __launch_bounds__(256) prep_b_kernel(GemmDesc g, __nv_bfloat16* 
 // C[b][i][j] = alpha (C32[i][j] + i C32[M + i][j]) + beta C[b][i][j]; grid (column chunks, rows, batch)
 __global__ void __launch_bounds__(256) gather_c_kernel(GemmDesc g, const float* C32, int Mp, int Np) {
   const int b = blockIdx.z, i = blockIdx.y;
+  if (skipped(g.skip, g.skip_mod, b)) return;
   const float* top = C32 + ((long long)b * Mp + i) * Np;
   const float* bot = C32 + ((long long)b * Mp + g.M + i) * Np;
   cplx* Cb = g.Cptr ? g.Cptr[b] : g.C + (long long)b * g.sC;
@@ -393,7 +399,8 @@ size_t split_workspace_bytes(int M, int N, int K, int batch) {
 
 template <int BN>
 static int launch_tc(const CUtensorMap& mA, const CUtensorMap& mB, float* C32, int Mp, int Np, int Kp,
-                     int batch, double algo_flops, unsigned* err, cudaStream_t st) {
+                     int batch, double algo_flops, unsigned* err, const int* skip, int skip_mod,
+                     cudaStream_t st) {
   using Cfg = TileCfg<BN>;
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
@@ -407,13 +414,14 @@ static int launch_tc(const CUtensorMap& mA, const CUtensorMap& mB, float* C32, i
   prof_add_tc_executed(flops);
   IPEPS_LAUNCH(K_TC_GEMM, algo_flops > 0.0 ? algo_flops : flops, st,
                tc_gemm_kernel<BN><<<grid, THREADS, Cfg::SMEM_BYTES, st>>>(mA, mB, C32, Np, (long long)Mp * Np,
-                                                                        Kp / BK, err));
+                                                                        Kp / BK, err, skip, skip_mod));
   IPEPS_CUDA_TRY(cudaGetLastError());
   return 0;
 }
 
 int gemm_bf16_raw(const void* A3, const void* B3t, float* C32, int Mp, int Np, int Kp, int batch,
-                  int bn, double algo_flops, unsigned* err, cudaStream_t st) {
+                  int bn, double algo_flops, unsigned* err, cudaStream_t st, const int* skip,
+                  int skip_mod) {
   if ((bn != 128 && bn != 256) || Mp % BM || Np % bn || Kp % BK || batch < 1 || batch > 65535)
     return cuda_fail(cudaErrorInvalidValue, "tc gemm shape", __FILE__, __LINE__);
   if (((uintptr_t)A3 & 15) || ((uintptr_t)B3t & 15) || ((uintptr_t)C32 & 15))
@@ -421,8 +429,8 @@ int gemm_bf16_raw(const void* A3, const void* B3t, float* C32, int Mp, int Np, i
   CUtensorMap mA, mB;
   if (int rc = make_map(&mA, A3, Mp, Kp, batch, BM)) return rc;
   if (int rc = make_map(&mB, B3t, Np, Kp, batch, bn)) return rc;
-  return bn == 256 ? launch_tc<256>(mA, mB, C32, Mp, Np, Kp, batch, algo_flops, err, st)
-                   : launch_tc<128>(mA, mB, C32, Mp, Np, Kp, batch, algo_flops, err, st);
+  return bn == 256 ? launch_tc<256>(mA, mB, C32, Mp, Np, Kp, batch, algo_flops, err, skip, skip_mod, st)
+                   : launch_tc<128>(mA, mB, C32, Mp, Np, Kp, batch, algo_flops, err, skip, skip_mod, st);
 }
 
 int zgemm_split_bf16(const GemmDesc& g, void* work, size_t work_bytes, unsigned* err, cudaStream_t st) {
@@ -451,7 +459,8 @@ int zgemm_split_bf16(const GemmDesc& g, void* work, size_t work_bytes, unsigned*
   IPEPS_LAUNCH(K_TC_PREP, 0, st, prep_b_kernel<<<pb, pblk, 0, st>>>(g, B3, Np, Kp));
   IPEPS_CUDA_TRY(cudaGetLastError());
   const double algo = 8.0 * g.M * (double)g.N * g.K * g.batch;   // the complex product's own flops
-  if (int rc = gemm_bf16_raw(A3, B3, C32, Mp, Np, Kp, g.batch, bn, algo, err, st)) return rc;
+  if (int rc = gemm_bf16_raw(A3, B3, C32, Mp, Np, Kp, g.batch, bn, algo, err, st, g.skip, g.skip_mod))
+    return rc;
   const dim3 gc((g.N + 255) / 256, g.M, g.batch);
   IPEPS_LAUNCH(K_TC_PREP, 0, st, gather_c_kernel<<<gc, 256, 0, st>>>(g, C32, Mp, Np));
   IPEPS_CUDA_TRY(cudaGetLastError());

@@ -13,6 +13,7 @@ int zgemm_split_bf16(const GemmDesc& g, void* work, size_t work_bytes, unsigned*
 // algo_flops: the algorithmic flops this launch serves (recorded by the launch accounting; <= 0
 // records the executed 2 Mp Np Kp batch instead)
 int gemm_bf16_raw(const void* A3, const void* B3t, float* C32, int Mp, int Np, int Kp, int batch,
-                  int bn, double algo_flops, unsigned* err, cudaStream_t st);
+                  int bn, double algo_flops, unsigned* err, cudaStream_t st, const int* skip = nullptr,
+                  int skip_mod = 0);
 }  // namespace tc
 }  // namespace ipeps
