@@ -4,16 +4,20 @@
 Workload (one GPU): three instances of the dilated hard-core boson lattice (J = V = 1,
 h = 1, 5, 10), PEPS bond dimension D = 3, environment chi = 18, second-order Trotter steps of
 dt = 0.05 with the CTMRG environment converged to 1e-10 and the observables read out every 0.25
-(every 5 Trotter steps).  One bench step is one such readout interval for all three instances:
-5 Trotter steps (7 bond updates each), CTMRG to convergence, measurement.
+(every 5 Trotter steps), from t = 0 to t = 5.  One bench step is one such readout interval for all
+three instances: 5 Trotter steps (7 bond updates each), CTMRG to convergence, measurement.  The
+steps walk the trajectory in order and start again from the CDW state after t = 5.
 
 metric  Trotter steps per second, summed over instances (and ranks), CTMRG and readout included
-value   device-resident state, timed with CUDA events on the library's stream
-e2e     the same steps through the public API with the state copied in from pinned host memory
-        (ipeps_set_tensors) and the tensors and observables copied back every step
-roofline  the kernel class with the largest share of the timed region, algorithmic flops per
-          launch over its event-timed average duration, against the FP64 rate measured in this run
-cpu_baseline  the FP64 oracle on the host, one instance, a bounded sample of the same workload
+value   device-resident state, timed with CUDA events on the library's stream, per-launch events off
+e2e     the same K steps through the public API with the state copied in from pinned host memory
+        (ipeps_set_tensors) and the tensors, bond weights and observables copied back every step
+roofline  from a separate profiled pass (per-launch CUDA events): the kernel class with the largest
+          share, algorithmic flops per launch over its average duration, against GB300's FP64 rate
+contraction  the standalone CTMRG contraction workload (random tensors, D = 6, chi = 72, split
+          precision, 20 sweeps): algorithmic contraction TFLOP/s and the tcgen05 GEMM's own
+          executed / algorithmic TFLOP/s against the measured BF16 peak
+cpu_baseline  the FP64 oracle on the host: one whole readout interval of one instance
 
 --impl reference times the oracle (this workload's reference implementation) instead.
 Multi-GPU (torchrun): independent replicas, one per rank, no collectives on the data path.
@@ -40,7 +44,6 @@ UNIT = "Trotter steps/s"
 WORKLOAD = ("iPEPS MBL quench, D=3 chi=18, 3 instances (J=V=1, h=1,5,10), 2nd-order dt=0.05, "
             "CTMRG to 1e-10 + readout every 0.25")
 L2_FLUSH_BYTES = 256 << 20
-REFERENCE_SWEEPS_PER_READOUT = 87.0
 
 
 def parse():
@@ -49,7 +52,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=6)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("native", "reference"), default="native")
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--contraction-D", type=int, default=6,
+                    help="bond dimension of the contraction sub-benchmark in the default line (0: skip)")
     ap.add_argument("--requests", type=int, default=32, help="serve workload: requests in the stream")
     ap.add_argument("--workload", choices=("quench", "ctmrg", "sweep", "serve"), default="quench",
                     help="quench: the Trotter+CTMRG readout workload (default); ctmrg: the standalone "
@@ -108,61 +112,105 @@ class Clocks:
 
 
 # ----------------------------------------------------------------------------- oracle sample
-ORACLE_SAMPLE = ("one instance (h=5), 5 second-order Trotter steps from t=0, 2 CTMRG sweeps from "
-                 "the traced start and one readout; scaled to a full step with the GPU run's mean "
-                 "sweeps per readout")
-
-
-def oracle_sample(sweeps_per_readout, threads=1):
-    """Time the oracle on a bounded sample with `threads` BLAS/OpenMP threads; returns (steps/s,
-    sample seconds, parts)."""
-    code = r"""
+ORACLE_STATE_T = 0.75          # the sampled readout interval is t = 0.75 -> 1.0 of the h = 5 instance
+ORACLE_CODE = r"""
 import json, sys, time
 sys.path.insert(0, %r)
-from oracle import ctmrg, evolve, measure
+from oracle import ctmrg, evolve, measure, model, su
 p = dict(J=1.0, V=1.0, h=5.0, D=3, chi=18, order=2, dt=0.05)
-t0 = time.perf_counter(); GA, GB, lam, _ = evolve.evolve_tensors(p, 5); t1 = time.perf_counter()
+mode = sys.argv[1]
+# state at t = 0.75 and its converged environment (preparation, not timed)
+GA, GB, lam, _ = evolve.evolve_tensors(p, int(round(%r / p['dt'])))
 A, B, a = evolve.ctm_state(GA, GB, lam)
-env = ctmrg.init_env(a, 2, 2, 18, 3)
-t2 = time.perf_counter()
-for _ in range(2):
-    env = ctmrg.sweep(a, env, 18)
-t3 = time.perf_counter()
-measure.observables(A, B, env, 1.0, 1.0, 5.0)
-t4 = time.perf_counter()
-print(json.dumps(dict(su=t1 - t0, sweep=(t3 - t2) / 2, measure=t4 - t3, total=t4 - t0)))
-""" % ROOT
+env0, _, _ = ctmrg.ctmrg(a, ctmrg.init_env(a, 2, 2, 18, 3), 18, tol=1e-10, max_sweeps=500)
+seq = su.trotter_sequence(2, 0.05)
+gates = {d: model.gate(1.0, 1.0, 5.0, d) for _, d in seq}
+def interval(full):
+    t0 = time.perf_counter()
+    g = (GA, GB, lam)
+    for _ in range(5):
+        g = su.trotter_step(g[0], g[1], g[2], gates, 2, 0.05)[:3]
+    t1 = time.perf_counter()
+    A2, B2, a2 = evolve.ctm_state(*g)
+    if full:
+        env, n, _ = ctmrg.ctmrg(a2, env0.copy(), 18, tol=1e-10, max_sweeps=500)
+    else:
+        env, n = ctmrg.sweep(a2, env0.copy(), 18), 1
+    t2 = time.perf_counter()
+    measure.observables(A2, B2, env, 1.0, 1.0, 5.0)
+    t3 = time.perf_counter()
+    return dict(su=t1 - t0, ctmrg=t2 - t1, sweeps=n, readout=t3 - t2, total=t3 - t0)
+warm, count = int(sys.argv[2]), int(sys.argv[3])
+for _ in range(warm):
+    for _ in range(5):
+        su.trotter_step(GA, GB, lam, gates, 2, 0.05)
+print(json.dumps([interval(mode == "full") for _ in range(count)]))
+"""
+
+
+def oracle_run(mode, count=1, warmup=0, threads=1):
+    """Run the oracle in one subprocess with ``threads`` BLAS/OpenMP threads and return ``count``
+    timed samples (after ``warmup`` untimed repetitions of the 5 Trotter steps).  mode "full": one
+    whole readout interval of one instance (t = 0.75 -> 1.0, h = 5: 5 second-order Trotter steps,
+    CTMRG warm-started from the t = 0.75 environment and converged to 1e-10, full readout), timed
+    end to end; mode "parts": the same 5 Trotter steps, ONE CTMRG sweep and the full readout, each
+    timed.  The state at t = 0.75 and its converged environment are prepared once, untimed."""
     n = str(int(threads))
     env = dict(os.environ, OMP_NUM_THREADS=n, OPENBLAS_NUM_THREADS=n, MKL_NUM_THREADS=n)
-    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
-                         timeout=600)
-    r = json.loads(out.stdout.strip().splitlines()[-1])
-    per_instance = r["su"] + sweeps_per_readout * r["sweep"] + r["measure"]
-    rate = STEPS_PER_READOUT / per_instance          # Trotter steps/s for one instance
-    return rate, r["total"], r
+    out = subprocess.run([sys.executable, "-c", ORACLE_CODE % (ROOT, ORACLE_STATE_T), mode, str(warmup),
+                          str(count)], capture_output=True, text=True, env=env, timeout=3600)
+    if out.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+ORACLE_SAMPLE = ("one whole readout interval of one instance, timed end to end: t = 0.75 -> 1.0 of "
+                 "the h = 5 instance (5 second-order Trotter steps, CTMRG warm-started from the "
+                 "t = 0.75 environment and converged to 1e-10, full readout); the state and its "
+                 "t = 0.75 environment are prepared untimed")
+
+
+def oracle_sweeps_per_readout():
+    """The oracle's own mean number of CTMRG sweeps per warm-started readout on this workload
+    (t in (0, 5], h = 1, 5, 10), as recorded in its stored trajectories."""
+    counts = []
+    for h in HS:
+        g = json.load(open(os.path.join(ROOT, "tests", "golden", "quench_d3_h%d_oracle.json" % int(h))))
+        counts += [r["ctm_sweeps"] for r in g["rows"][1:]]
+    return float(np.mean(counts)), len(counts)
 
 
 def reference_main(args):
+    """The oracle as the reference arm.  A whole readout interval of the oracle takes ~20 s, so a
+    step times its three parts separately -- 5 Trotter steps, one CTMRG sweep and the full readout
+    of the interval t = 0.75 -> 1.0 (h = 5) -- and the line composes them into a readout interval
+    with the oracle's own mean sweeps per readout on this workload."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    # CTMRG sweeps per readout of this workload (same tolerance and stall rule as the oracle's),
-    # mean over instances measured on the GPU path: the oracle needs as many
-    mean_sweeps = REFERENCE_SWEEPS_PER_READOUT
-    times = []
-    samples = []
-    for i in range(args.warmup + args.steps):
-        rate, sec, r = oracle_sample(mean_sweeps)
-        if i >= args.warmup:
-            times.append(STEPS_PER_READOUT / rate * len(HS))
-            samples.append(rate)
-    value = len(HS) * STEPS_PER_READOUT * len(times) / sum(times)
+    t0 = time.perf_counter()
+    parts = oracle_run("parts", count=args.steps, warmup=args.warmup)
+    wall = time.perf_counter() - t0
+    mean_sweeps, nrows = oracle_sweeps_per_readout()
+    t_su = float(np.mean([q["su"] for q in parts]))
+    t_sweep = float(np.mean([q["ctmrg"] for q in parts]))
+    t_read = float(np.mean([q["readout"] for q in parts]))
+    t_interval = t_su + mean_sweeps * t_sweep + t_read          # one instance, one readout interval
+    value = STEPS_PER_READOUT / t_interval
+    sample = ("per step, timed separately on one core: the 5 Trotter steps, one CTMRG sweep and the "
+              "full readout of the interval t = 0.75 -> 1.0 (h = 5); composed into a readout interval "
+              "as su + %.1f sweeps + readout, %.1f being the oracle's own mean sweeps per warm "
+              "readout over its %d stored readouts of this workload (t in (0, 5], h = 1, 5, 10)"
+              % (mean_sweeps, mean_sweeps, nrows))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "l2": "host run"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": ORACLE_SAMPLE + "; %.0f sweeps per readout assumed" % mean_sweeps},
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t_interval * len(HS), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "l2": "host run"},
+            "composed": {"su_s": t_su, "sweep_s": t_sweep, "readout_s": t_read,
+                         "sweeps_per_readout": mean_sweeps,
+                         "run_seconds": wall, "timed_seconds": sum(q["total"] for q in parts)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -194,6 +242,61 @@ def replica_throughput(units_per_rank, world, max_ms):
 
 
 # ----------------------------------------------------------------------------- native arm
+CYCLE = 20                     # readout intervals from t = 0 to t = 5 (the workload's trajectory)
+PROFILED_STEPS = 10            # steps of the separate profiled pass (kernel shares, roofline)
+FP64_PEAK_TFLOPS = 1.25        # GB300 FP64 (no FP64 tensor path): 152 SMs x 2 DFMA/clk x 2.07 GHz x 2
+
+
+class Quench:
+    """The quench workload on one handle: a step is one readout interval (5 Trotter steps, CTMRG to
+    convergence, readout) of the three instances; the trajectory runs t = 0 -> 5 and starts again
+    from the CDW state after 20 intervals."""
+
+    def __init__(self, pkg, stream):
+        B = len(HS)
+        self.sim = pkg.IPEPS([J] * B, [V] * B, list(HS), D=D, chi=CHI, order=ORDER, dt=DT,
+                             stream=stream.cuda_stream)
+        GA, GB = self.sim.get_tensors()
+        self.initial = (GA, GB, self.sim.get_lambda())
+
+    def restart(self, state=None):
+        """Back to t = 0 (from host buffers: the CDW tensors), traced start, t = 0 readout."""
+        GA, GB, lam = state if state is not None else self.initial
+        self.sim.set_tensors(GA, GB, lam)
+        self.sim.ctmrg_reset()
+        self.sim.ctmrg_converge(tol=TOL, max_sweeps=MAX_SWEEPS, allow_noconv=True)
+        self.sim.measure()
+
+    def interval(self):
+        self.sim.trotter_step(STEPS_PER_READOUT, sync=False)
+        sw, dl, rc = self.sim.ctmrg_converge(tol=TOL, max_sweeps=MAX_SWEEPS, allow_noconv=True)
+        return self.sim.measure(), sw
+
+    def step(self, i):
+        if i % CYCLE == 0:
+            self.restart()
+        return self.interval()
+
+
+def timed_pass(q, steps, stream, flush, torch):
+    """K steps from t = 0, each bracketed by CUDA events on the library's stream (L2 flushed before
+    each step, outside the events).  Returns (total ms, per-step ms, per-step sweeps)."""
+    total, step_ms, sweeps = 0.0, [], []
+    for i in range(steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, sw = q.step(i)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        total += ms
+        step_ms.append(ms)
+        sweeps.append([int(x) for x in sw])
+    return total, step_ms, sweeps
+
+
 def native_main(args):
     import torch
     import paper_1910_11359_gb300 as pkg
@@ -209,125 +312,194 @@ def native_main(args):
     stream = torch.cuda.Stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     B = len(HS)
-    sim = pkg.IPEPS([J] * B, [V] * B, list(HS), D=D, chi=CHI, order=ORDER, dt=DT,
-                    stream=stream.cuda_stream)
-
-    def step():
-        sim.trotter_step(STEPS_PER_READOUT, sync=False)
-        sw, dl, rc = sim.ctmrg_converge(tol=TOL, max_sweeps=MAX_SWEEPS, allow_noconv=True)
-        return sim.measure(), sw
-
     with torch.cuda.stream(stream):
-        sim.ctmrg_converge(tol=TOL, max_sweeps=MAX_SWEEPS, allow_noconv=True)
-        sim.measure()
-        for _ in range(args.warmup):
-            step()
+        q = Quench(pkg, stream)
+        for i in range(args.warmup):
+            q.step(i)
         torch.cuda.synchronize()
+
+        # ---- value: device-resident state, profiling off
         clocks = Clocks(local)
         clocks.start()
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()
         launches0 = pkg.launch_count()
-        pkg.profile_enable(True)
-        total_ms = 0.0
-        sweeps = []
-        step_ms = []
-        sweep_ms = []                                         # per step: time / sweeps run
-        last = None
-        for _ in range(args.steps):
-            flush.fill_(1.0)                                  # L2 flush between timed steps
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            last, sw = step()
-            e1.record(stream)
-            e1.synchronize()
-            ms = e0.elapsed_time(e1)
-            total_ms += ms
-            step_ms.append(ms)
-            sweep_ms.append(ms / max(1, max(int(s) for s in sw)))
-            sweeps.extend(int(s) for s in sw)
+        total_ms, step_ms, sweeps = timed_pass(q, args.steps, stream, flush, torch)
         torch.cuda.synchronize()
-        prof = pkg.profile_read()
-        pkg.profile_enable(False)
         launches = pkg.launch_count() - launches0
         total_ms = reduce_max_ms(total_ms, dist, "cuda")
         if dist is not None:
             dist.barrier()
         clk = clocks.stop()
         value = replica_throughput(B * STEPS_PER_READOUT * args.steps, world, total_ms)
+        sweep_ms = [ms / max(1, max(sw)) for ms, sw in zip(step_ms, sweeps)]
 
-        # end to end through the public API with host buffers (pinned), copies inside the timing
-        GA, GB = sim.get_tensors()
-        lam = sim.get_lambda()
-        hGA = torch.from_numpy(GA.view(np.float64)).pin_memory().numpy().view(np.complex128)
-        hGB = torch.from_numpy(GB.view(np.float64)).pin_memory().numpy().view(np.complex128)
+        # ---- e2e: the same K steps through the public API with the state in pinned host memory:
+        # every step copies the tensors in (ipeps_set_tensors), runs the interval and copies the
+        # tensors, bond weights and observables back
+        GA0, GB0, lam0 = q.initial
+        hGA = torch.empty(GA0.shape + (2,), dtype=torch.float64).pin_memory().numpy().view(np.complex128)[..., 0]
+        hGB = torch.empty(GB0.shape + (2,), dtype=torch.float64).pin_memory().numpy().view(np.complex128)[..., 0]
+        hlam = torch.empty(lam0.shape, dtype=torch.float64).pin_memory().numpy()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for _ in range(args.e2e_steps):
-            sim.set_tensors(hGA, hGB, lam)
-            obs, _ = step()
-            gA, gB = sim.get_tensors()
-            hGA[...] = gA
-            hGB[...] = gB
-            lam = sim.get_lambda()
+        for i in range(args.steps):
+            flush.fill_(1.0)                     # the same L2 flush as the device-timed steps
+            if i % CYCLE == 0:
+                hGA[...], hGB[...], hlam[...] = GA0, GB0, lam0
+                q.restart((hGA, hGB, hlam))
+            q.sim.set_tensors(hGA, hGB, hlam)
+            obs, _ = q.interval()
+            gA, gB = q.sim.get_tensors()
+            hGA[...], hGB[...] = gA, gB
+            hlam[...] = q.sim.get_lambda()
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
-        e2e_value = B * STEPS_PER_READOUT * args.e2e_steps * world / e2e_s
-        h2d = 2 * GA.nbytes + lam.nbytes
-        d2h = 2 * GA.nbytes + lam.nbytes + B * 88
-    sim.close()
+        e2e_value = B * STEPS_PER_READOUT * args.steps * world / e2e_s
+        h2d = 2 * GA0.nbytes + lam0.nbytes
+        d2h = 2 * GA0.nbytes + lam0.nbytes + B * 88
 
-    # roofline of the dominant kernel class
+        # ---- profiled pass (not timed for value): per-class CUDA-event times on the library's
+        # stream, for the kernel shares and the roofline of the dominant kernel
+        nprof = min(args.steps, PROFILED_STEPS)
+        torch.cuda.synchronize()
+        pkg.profile_enable(True)
+        prof_ms, _, _ = timed_pass(q, nprof, stream, flush, torch)
+        prof = pkg.profile_read()
+        pkg.profile_enable(False)
+        q.sim.close()
+
+        contraction = None
+        if rank == 0 and args.contraction_D > 0:
+            contraction = contraction_bench(pkg, torch, args.contraction_D, stream)
+
     dom = max(prof.items(), key=lambda kv: kv[1][0])
     name, (ms, flops, n) = dom
-    peak = pkg.fp64_peak_tflops()
+    probe = pkg.fp64_peak_tflops()
     achieved = flops / (ms * 1e-3) / 1e12 if ms > 0 else 0.0
     traffic = None
     tfile = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tfile):
         tj = json.load(open(tfile))
-        if tj.get("kernel") == name and tj.get("workload") == WORKLOAD:
+        if tj.get("kernel") == name and tj.get("workload") == WORKLOAD and tj.get("source_sha") == _kernel_sha():
             traffic = tj.get("dram_bytes_per_launch")
-    shares = {k: round(v[0] / total_ms, 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])
+    shares = {k: round(v[0] / prof_ms, 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])
               if v[0] > 0}
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return 0
-    mean_sweeps = float(np.mean(sweeps)) if sweeps else 10.0
-    cpu_rate, cpu_sec, cpu_parts = oracle_sample(mean_sweeps)
+    flat = [x for sw in sweeps for x in sw]
+    full = oracle_run("full")[0]
     ncores = os.cpu_count() or 1
-    all_rate, all_sec, _ = oracle_sample(mean_sweeps, threads=ncores)
+    full_all = oracle_run("full", threads=ncores)[0]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "instances_per_gpu": B, "D": D, "chi": CHI,
                    "parallelism": "replicas" if world > 1 else "single",
+                   "trajectory": "steps cycle through the readout intervals of t = 0 -> 5 "
+                                 "(interval i covers t = 0.25 (i mod 20) -> 0.25 (i mod 20 + 1); "
+                                 "every 20 steps the state restarts from the CDW)",
                    "l2": "flushed (256 MiB write) between timed steps",
-                   "mean_ctm_sweeps_per_readout": mean_sweeps},
+                   "mean_ctm_sweeps_per_readout": float(np.mean(flat)),
+                   "physics": "past t ~ 0.5 the D = 3 state's accumulated discarded weight exceeds "
+                              "the ~1e-3 the paper accepts (0.1 by t = 2): the numbers past that "
+                              "time are outputs of the method, not converged physics"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(d2h)},
-        "roofline": {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak if peak else None,
-                     "traffic": traffic, "launches": n, "avg_launch_us": 1e3 * ms / max(n, 1),
-                     "peak_source": "FP64 FMA rate measured in this run (no FP64 tensor path)"},
+                "d2h_bytes_per_step": int(d2h), "steps": args.steps,
+                "timing": "wall clock over the same K steps, L2 flushed before each step"},
+        "roofline": {"bound": "alu", "kernel": name, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+                     "launches": n, "avg_launch_us": 1e3 * ms / max(n, 1),
+                     "peak_source": "GB300 FP64 rate from the recipe's unit counts and clock "
+                                    "(1.25 TFLOP/s; no FP64 tensor path); the FP64 FMA probe "
+                                    "measured %.3f TFLOP/s in this run" % probe,
+                     "timing": "CUDA events per launch in a separate profiled pass of %d steps "
+                               "(value itself is timed with the per-launch events off)" % nprof},
         "kernel_time_share": shares,
         "latency_ms": latency_summary(step_ms, sweep_ms),
         "gpu_launches": int(launches),
         "clocks": clk,
-        "cpu_baseline": {"value": cpu_rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": ORACLE_SAMPLE, "sample_seconds": round(cpu_sec, 2),
-                         "parts_s": {k: round(v, 3) for k, v in cpu_parts.items()},
-                         "all_cores": {"value": all_rate, "cores": ncores,
-                                       "sample_seconds": round(all_sec, 2)}},
+        "cpu_baseline": {"value": STEPS_PER_READOUT / full["total"], "unit": UNIT, "cores": 1,
+                         "kind": "oracle", "sample": ORACLE_SAMPLE,
+                         "sample_seconds": round(full["total"], 2), "sweeps": full["sweeps"],
+                         "parts_s": {k: round(full[k], 3) for k in ("su", "ctmrg", "readout")},
+                         "all_cores": {"value": STEPS_PER_READOUT / full_all["total"], "cores": ncores,
+                                       "sample_seconds": round(full_all["total"], 2)},
+                         "note": "the sampled interval needs %d CTMRG sweeps; the GPU run averaged "
+                                 "%.1f sweeps per readout over its steps" % (full["sweeps"], float(np.mean(flat)))},
     }
+    if contraction is not None:
+        line["contraction"] = contraction
     print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def _kernel_sha():
+    """Hash of the CUDA sources, to tell whether a stored ncu traffic figure still describes them."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1910_11359_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def contraction_bench(pkg, torch, D, stream, sweeps=20):
+    """The standalone CTMRG contraction workload (random (4, D, D, D, D) tensors, chi = 2 D^2,
+    split-precision contractions, 20 sweeps from the traced start): sweeps/s and algorithmic
+    contraction TFLOP/s timed with the per-launch events off, then the tcgen05 GEMM's own
+    executed and algorithmic TFLOP/s from a profiled pass of 4 sweeps."""
+    from inputs import random_ctmrg_tensors
+    chi = 2 * D * D
+    A, B = random_ctmrg_tensors(D)
+    sim = pkg.IPEPS([1.0], [1.0], [5.0], D=D, chi=chi, order=2, dt=0.05, precision=pkg.SPLIT_BF16X3,
+                    stream=stream.cuda_stream)
+    sim.set_tensors(A[None], B[None], None)
+    sim.ctmrg_converge(tol=0.0, max_sweeps=2)
+    sim.ctmrg_reset()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.ctmrg_converge(tol=0.0, max_sweeps=sweeps)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    sim.ctmrg_reset()
+    pkg.profile_enable(True)
+    sim.ctmrg_converge(tol=0.0, max_sweeps=4)
+    prof = pkg.profile_read()
+    executed = pkg.profile_tc_executed()
+    pkg.profile_enable(False)
+    sim.close()
+    peaks_file = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peaks = json.load(open(peaks_file)) if os.path.exists(peaks_file) else {}
+    bf16 = peaks.get("bf16_tflops", 1900.0)
+    tms, tfl, tn = prof.get("tc_gemm_bf16", (0.0, 0.0, 0))
+    tot = sum(v[0] for v in prof.values())
+    algo = contraction_flops_per_sweep(D, chi) * sweeps
+    return {"workload": "CTMRG contraction, random (4,D,D,D,D) N(0,1)+iN(0,1), D=%d chi=%d, %d sweeps "
+                        "from the traced start, BF16x3 split contractions, FP64 projectors" % (D, chi, sweeps),
+            "sweeps_per_s": sweeps / (ms * 1e-3),
+            "contraction_tflops": algo / (ms * 1e-3) / 1e12,
+            "contraction_frac_of_bf16_peak": algo / (ms * 1e-3) / 1e12 / bf16,
+            "tc_gemm": None if not tn else {
+                "launches": tn, "avg_launch_us": 1e3 * tms / tn,
+                "algorithmic_tflops": tfl / (tms * 1e-3) / 1e12,
+                "executed_tflops": executed / (tms * 1e-3) / 1e12,
+                "peak": bf16, "frac_algorithmic": tfl / (tms * 1e-3) / 1e12 / bf16,
+                "frac_executed": executed / (tms * 1e-3) / 1e12 / bf16,
+                "share_of_sweep": tms / tot if tot else None,
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)" if peaks else "fallback 1900"},
+            "kernel_time_share": {k: round(v[0] / tot, 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])
+                                  if v[0] > 0 and tot > 0}}
 
 
 def contraction_flops_per_sweep(D, chi):

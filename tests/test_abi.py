@@ -84,6 +84,8 @@ def test_null_handles_and_bad_sizes_fail_cleanly(lib):
         lambda: lib.ipeps_corner_spectrum(vp(None), 0, 0, 0, vp(None)),
         lambda: lib.ipeps_get_lambda(vp(None), vp(None)),
         lambda: lib.ipeps_get_tensors(vp(None), vp(None), vp(None)),
+        lambda: lib.ipeps_get_env(vp(None), 0, vp(None), vp(None)),
+        lambda: lib.ipeps_set_env(vp(None), 0, vp(None), vp(None)),
         # m < n, and a batch beyond the allocation-free entry point's fixed scratch
         lambda: lib.ipeps_kernel_svd(3, 5, 1, vp(1), vp(None), vp(1), vp(None), ctypes.c_double(1e-14),
                                      10, vp(None), vp(None)),
@@ -94,3 +96,15 @@ def test_null_handles_and_bad_sizes_fail_cleanly(lib):
         assert call() == 1
         assert len(lib.ipeps_last_error(vp(None)) or b"") > 5
     assert lib.ipeps_destroy(vp(None)) == 0
+
+
+def test_noalloc_svd_rejects_blocks_beyond_shared_memory(lib):
+    """The allocation-free SVD keeps the columns in shared memory only: a block too tall for the
+    cluster's shared memory, which ipeps_kernel_svd still serves from a global-memory column buffer,
+    is refused with IPEPS_EUNSUPPORTED (8) before any device call."""
+    vp = ctypes.c_void_p
+    lib.ipeps_last_error.restype = ctypes.c_char_p
+    rc = lib.ipeps_kernel_svd_noalloc(2592, 80, 1, vp(1), vp(None), vp(1), vp(None),
+                                      ctypes.c_double(1e-14), 10, vp(None), vp(None))
+    assert rc == 8
+    assert b"shared memory" in lib.ipeps_last_error(vp(None))

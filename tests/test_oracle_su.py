@@ -1,11 +1,11 @@
 """Pins for oracle/su.py (simple update, Trotter sequences).
 
 * D = 1: the simple update reduces to propagating a product state; an independent product-state
-  script (kron, gate, rank-1 SVD) must give the same local densities (SURVEY pin P6).
+  script (kron, gate, rank-1 SVD) must give the same local densities.
 * One bond update from the CDW at D = 4 is exact: the new bond weights are the Schmidt values of
-  the exact two-site state and nothing is discarded (pin P8 i), for every bond orientation.
-* J = 0: the CDW is an eigenstate; every bond spectrum stays (1, 0, ...) (pin P1).
-* J -> -J (sublattice gauge) and h -> -h (auxiliary flip) leave every bond spectrum unchanged (P3).
+  the exact two-site state and nothing is discarded, for every bond orientation.
+* J = 0: the CDW is an eigenstate; every bond spectrum stays (1, 0, ...).
+* J -> -J (sublattice gauge) and h -> -h (auxiliary flip) leave every bond spectrum unchanged.
 """
 import numpy as np
 import pytest
