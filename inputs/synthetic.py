@@ -10,6 +10,8 @@ Workloads (shapes and parameters of the paper's runs, restated for the hard-core
   N(0,1) + i N(0,1) entries scaled to unit largest singular value of the 4 x D^4 matricisation;
   D in {4, 5, 6}, chi = 2 D^2, 20 sweeps.  A uses seed 0, B seed 1.
 * DISORDER_SWEEP -- batched disorder sweep of 64 instances of mixed D (disorder_sweep_points).
+* QUENCH_DA3 -- d_A = 3 disorder levels (d = 6), D = 3, chi = 9, J = V = 1, h = 5, second-order
+  Trotter, dt = 0.05 to t = 0.5, measured every 0.1.
 """
 import numpy as np
 
@@ -18,6 +20,9 @@ QUENCH_D2 = dict(J=1.0, V=1.0, h=5.0, D=2, chi=8, order=1, dt=0.02, t_max=1.0, m
 QUENCH_D3 = dict(J=1.0, V=1.0, hs=(1.0, 5.0, 10.0), D=3, chi=18, order=2, dt=0.05, t_max=5.0,
                meas_every=0.25, tol=1e-10)
 RANDOM_CTMRG = dict(Ds=(4, 5, 6), sweeps=20, seeds=(0, 1))
+# three disorder levels (field values h, 0, -h per site, d = 6), the paper's next step up in d_A
+QUENCH_DA3 = dict(J=1.0, V=1.0, h=5.0, D=3, chi=9, order=2, dt=0.05, t_max=0.5, meas_every=0.1,
+                  tol=1e-10, d_A=3)
 
 
 def disorder_sweep_points(n=64, seed=4):

@@ -19,6 +19,7 @@ Quantities:
               where the two chi-legs of each edge tensor sit on equivalent cuts; used for the Ising
               pin, not reported for the checkerboard state.
   purity      Tr(rho^2) / Tr(rho)^2 of the one-site RDM (Renyi-2 entropy = -ln purity).
+  renyi       Renyi entropies S_1, S_1/2, S_2 of the physical one-site RDM (auxiliary traced out).
 
 Parity: pinned by tests/test_oracle_ctmrg.py (Ising magnetisation, bond energy and free energy;
 dimer states; brute-force tori) and tests/test_oracle_evolve.py (J = 0, short-time closed form,
@@ -88,6 +89,25 @@ def expect2(rho, O):
     return num / den
 
 
+def physical_rdm(rho, d_A):
+    """One-site RDM of the physical boson alone: the auxiliary level traced out of rho[s, s'] with
+    s = n * d_A + a, normalised to unit trace (2 x 2)."""
+    dp = rho.shape[0] // d_A
+    r = np.einsum('iaja->ij', rho.reshape(dp, d_A, dp, d_A))
+    return r / np.trace(r)
+
+
+def renyi(rho_phys, alpha):
+    """Renyi entropy S_alpha = ln(Tr rho^alpha) / (1 - alpha) of a normalised density matrix; the
+    von Neumann entropy -Tr rho ln rho for alpha = 1 (Sec. "Results for interacting case": Renyi
+    entropies of the one-site RDM of the physical site, bounded by ln d_p)."""
+    p = np.clip(np.linalg.eigvalsh(0.5 * (rho_phys + rho_phys.conj().T)), 0.0, None)
+    p = p[p > 0]
+    if alpha == 1.0:
+        return float(-np.sum(p * np.log(p)))
+    return float(np.log(np.sum(p ** alpha)) / (1.0 - alpha))
+
+
 def observables(A, B, env, J, V, h, d_A=2):
     """Observables of the checkerboard state (A at (0,0), B at (1,0)); all real FP64."""
     b, n, tau, _ = local_ops(d_A)
@@ -104,5 +124,7 @@ def observables(A, B, env, J, V, h, d_A=2):
     e_bonds += expect2(rho2_v(B, A, env, (0, 1), (0, 0)), hb).real
     energy = 0.5 * (e_bonds + h * (tnA + tnB))
     purA = (np.einsum('st,ts->', rA, rA) / np.trace(rA) ** 2).real
+    pA = physical_rdm(rA, d_A)
     return dict(nA=nA, nB=nB, imbalance=nA - nB, imbalance_rel=(nA - nB) / (nA + nB),
-                tauzA=tzA, tauzB=tzB, energy=energy, purityA=purA)
+                tauzA=tzA, tauzB=tzB, energy=energy, purityA=purA,
+                renyi1A=renyi(pA, 1.0), renyi_halfA=renyi(pA, 0.5), renyi2A=renyi(pA, 2.0))

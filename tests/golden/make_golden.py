@@ -5,9 +5,11 @@
     python tests/golden/make_golden.py quench_d3      -> tests/golden/quench_d3_h{1,5,10}_oracle.json
     python tests/golden/make_golden.py quench_d3@5    -> tests/golden/quench_d3_h5_oracle.json only
     python tests/golden/make_golden.py quench_d3:2@5  -> the same, stopped at t = 2
+    python tests/golden/make_golden.py quench_da3     -> tests/golden/quench_dA3_D3_oracle.json
 
-Workloads: inputs.QUENCH_D2 (D=2, chi=8, first order dt=0.02 to t=1, measured every 0.1) and
-inputs.QUENCH_D3 (D=3, chi=18, second order dt=0.05 to t=5, measured every 0.25, h in {1,5,10}).
+Workloads: inputs.QUENCH_D2 (D=2, chi=8, first order dt=0.02 to t=1, measured every 0.1),
+inputs.QUENCH_D3 (D=3, chi=18, second order dt=0.05 to t=5, measured every 0.25, h in {1,5,10}) and
+inputs.QUENCH_DA3 (d_A=3 disorder levels, D=3, chi=9, second order dt=0.05 to t=0.5, every 0.1).
 Every stored value is the oracle's; nothing here touches the CUDA path.
 """
 import json
@@ -20,14 +22,15 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 
-from inputs import QUENCH_D2, QUENCH_D3  # noqa: E402
+from inputs import QUENCH_D2, QUENCH_D3, QUENCH_DA3  # noqa: E402
 from oracle import evolve  # noqa: E402
 
 # at most this many sweeps for the stability probe of every readout (evolve.converge_and_measure)
 PROBE = 100
 
 KEYS = ("t", "nA", "nB", "imbalance", "tauzA", "tauzB", "energy", "purityA", "trunc_err_acc",
-        "ctm_sweeps", "ctm_delta", "ctm_stop", "c8_margin", "c8_level", "drift", "probe_sweeps")
+        "ctm_sweeps", "ctm_delta", "ctm_stop", "c8_margin", "c8_level", "drift", "probe_sweeps",
+        "renyi1A", "renyi_halfA", "renyi2A")
 
 
 def _val(v):
@@ -61,6 +64,11 @@ def run(name):
         t0 = time.time()
         out = evolve.run(p, tol=p["tol"], cold=True, probe_sweeps=PROBE)
         _dump(os.path.join(HERE, "quench_d2_cut1e-6_oracle.json"), p, out, time.time() - t0)
+    elif name == "quench_da3":
+        p = dict(QUENCH_DA3)
+        t0 = time.time()
+        out = evolve.run(p, tol=p["tol"], cold=True, probe_sweeps=PROBE)
+        _dump(os.path.join(HERE, "quench_dA3_D3_oracle.json"), p, out, time.time() - t0)
     elif name.startswith("quench_d3"):
         # "quench_d3" = the full workload; "quench_d3:T" stops at t = T (same trajectory, fewer points);
         # "quench_d3@H" writes only the instance with h = H (the instances are independent)
