@@ -10,8 +10,9 @@
  *
  * Model (Eq. Hanc in hard-core boson form, V/J = 2 Delta of Eq. Hori):
  *   H = sum_<ij> [ -J (b_i^+ b_j + h.c.) + V n_i n_j ] + h sum_i tau_i n_i,
- * tau_i the auxiliary level operator with eigenvalues +1, -1 (d_A = 2); local basis s = 2 n + a,
- * d = 4.  Two-site checkerboard unit cell: A on x + y even, B on x + y odd.
+ * tau_i the auxiliary level operator with eigenvalues 1 - 2 a / (d_A - 1), a = 0 .. d_A - 1
+ * (+1, -1 for d_A = 2); local basis s = n d_A + a, d = 2 d_A.  Two-site checkerboard unit cell: A on
+ * x + y even, B on x + y odd.
  *
  * Layouts (row-major, complex = interleaved (re, im) doubles):
  *   Gamma tensors  [batch][d][D][D][D][D], leg order (s, up, left, down, right)
@@ -42,14 +43,17 @@ enum { IPEPS_FP64 = 0, IPEPS_SPLIT_BF16X3 = 1, IPEPS_SPLIT_TF32X3 = 2 };
 
 typedef struct {
   int batch;                /* independent instances sharing the shapes below (>= 1) */
-  int d_A;                  /* auxiliary levels (number of disorder values); 2 */
+  int d_A;                  /* auxiliary levels = number of disorder values, 2..5 (field levels
+                               spaced uniformly in [-h, h], Sec. "Set up for iPEPS"); d = 2 d_A;
+                               d_A > 2 needs D^2 >= d */
   int D;                    /* PEPS bond dimension (>= 2) */
   int chi;                  /* environment bond dimension (>= D^2, Appendix) */
   int trotter_order;        /* 1 or 2 */
   double dt;                /* Trotter step */
-  int precision;            /* IPEPS_FP64 or IPEPS_SPLIT_BF16X3 (contractions on the tensor cores,
-                               FP64 projectors); IPEPS_SPLIT_TF32X3 is declared but this build
-                               returns IPEPS_EUNSUPPORTED for it */
+  int precision;            /* IPEPS_FP64; IPEPS_SPLIT_BF16X3 or IPEPS_SPLIT_TF32X3: the large
+                               contractions on the tcgen05 tensor cores as 3-term split products
+                               (two BF16 / TF32 terms per value, FP32 accumulation; relative error
+                               ~1e-5 / ~1e-7), projectors, simple update and readout in FP64 */
   unsigned long long seed;  /* seeds random starting vectors of iterative solvers */
   const double* J;          /* [batch] hopping, host, copied */
   const double* V;          /* [batch] nearest-neighbour interaction, host, copied */
@@ -71,6 +75,9 @@ typedef struct {
   double trunc_err_acc;     /* accumulated discarded weight of the simple update (A's bonds) */
   int ctm_sweeps;           /* sweeps of the last ctmrg_converge */
   double ctm_delta;         /* final corner-spectrum change of the last ctmrg_converge */
+  double renyi1A;           /* Renyi entropies S_1 (von Neumann), S_1/2, S_2 of the physical one-site */
+  double renyi_halfA;       /* RDM of A, the auxiliary traced out (Sec. "Results for interacting      */
+  double renyi2A;           /* case"; at most ln d_p = ln 2)                                           */
 } ipeps_obs;
 
 /* Create a handle with `batch` instances in the CDW (x) |+> product state (Sec. "Set up for iPEPS",
@@ -93,11 +100,12 @@ ipeps_status ipeps_trotter_step(ipeps_h h, int n_steps, double* trunc_err_out);
 /* CTMRG environment of the current tensors (Sec. "Set up for iPEPS", Readout; Appendix: chi >= D^2,
  * "sufficiently well converged").  Directional moves with full 2x2-block projectors; per instance,
  * sweeps until the normalised corner spectra change by less than tol, or until that change has
- * stalled at its rounding floor (no factor-2 improvement of its best value for 10 sweeps while the
- * best is below 1e-7); converged instances stop updating; at most max_sweeps sweeps.  tol <= 0 runs
- * exactly max_sweeps sweeps.  With precision IPEPS_SPLIT_BF16X3 the contractions leave a noise floor
- * near 1e-6 in the spectra: a positive tol below 1e-7 is raised to 1e-7 and the stall rule applies
- * once the best change is below 1e-5.  The first call starts from the traced
+ * stalled at its rounding floor (no factor-2 improvement of its best value for 10 sweeps while that
+ * best and the current change are below 1e-7, the current one within 4x of the best); converged
+ * instances stop updating; at most max_sweeps sweeps.  tol <= 0 runs exactly max_sweeps sweeps.  The
+ * split precisions leave a noise floor in the spectra: with IPEPS_SPLIT_BF16X3 a positive tol below
+ * 1e-7 is raised to 1e-7 and the stall threshold is 1e-5; with IPEPS_SPLIT_TF32X3 they are 1e-8 and
+ * 1e-6.  The first call starts from the traced
  * double layers, later calls from the previous environment.  sweeps_out: host int[batch] or NULL;
  * delta_out: host double[batch] or NULL (last change).  Returns IPEPS_ENOCONV when an instance
  * reached max_sweeps without converging (its environment is still usable). */

@@ -38,6 +38,15 @@ int ipeps_kernel_zgemm(int M, int N, int K, int batch, int opA, int opB,
 int ipeps_kernel_svd_noalloc(int m, int n, int batch, const double* A, double* U, double* S,
                              double* V, double tol, int max_sweeps, int* sweeps_out, void* stream);
 
+/* Orthonormal columns spanning those of X[b] (N x k, row-major, contiguous per problem) for
+ * b < batch, by column-scaled Cholesky QR: passes >= 2 (the first with a diagonal shift that keeps
+ * the factorisation defined, the others plain).  Columns whose norm is below 1e-14 of the largest
+ * count as zero and give zero columns of Q.  fail_out: host int[batch] (or NULL) receiving 1 where
+ * the factorisation broke down or the last pass still saw the columns off orthonormal by more than
+ * 1e-2 (Q is then not usable).  k <= 110.  Allocates its workspace; synchronising. */
+int ipeps_kernel_orth(int N, int k, int batch, const double* X, double* Q, int passes, int* fail_out,
+                      void* stream);
+
 /* Trotter gate exp(-i h_b delta) of the d = 4 dilated model (J, V, h as in ipeps_params),
  * computed on the device and copied to the HOST buffer out (16 x 16 complex, row index sA*4+sB).
  * Allocates and frees a small device buffer; synchronising. */

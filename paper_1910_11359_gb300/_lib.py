@@ -37,7 +37,9 @@ class Obs(ctypes.Structure):
                 ("imbalance", ctypes.c_double), ("tauzA", ctypes.c_double),
                 ("tauzB", ctypes.c_double), ("energy", ctypes.c_double),
                 ("purityA", ctypes.c_double), ("trunc_err_acc", ctypes.c_double),
-                ("ctm_sweeps", ctypes.c_int), ("ctm_delta", ctypes.c_double)]
+                ("ctm_sweeps", ctypes.c_int), ("ctm_delta", ctypes.c_double),
+                ("renyi1A", ctypes.c_double), ("renyi_halfA", ctypes.c_double),
+                ("renyi2A", ctypes.c_double)]
 
 
 _lib = None
@@ -47,7 +49,8 @@ EXPORTS = ["ipeps_init", "ipeps_set_tensors", "ipeps_trotter_step", "ctmrg_conve
            "ipeps_kernel_permute", "ipeps_kernel_svd", "ipeps_kernel_gate", "ipeps_launch_count",
            "ipeps_profile_enable", "ipeps_profile_classes", "ipeps_profile_name", "ipeps_profile_read",
            "ipeps_kernel_fp64_peak", "ipeps_kernel_svd_noalloc", "ipeps_kernel_zgemm_split",
-           "ipeps_get_env", "ipeps_set_env", "ipeps_profile_tc_executed", "ipeps_profile_counters"]
+           "ipeps_get_env", "ipeps_set_env", "ipeps_profile_tc_executed", "ipeps_profile_counters",
+           "ipeps_kernel_orth", "ipeps_kernel_zgemm_split_tf32"]
 
 
 def lib():
@@ -89,9 +92,11 @@ def lib():
     L.ipeps_profile_read.argtypes = [dp, dp, P(ctypes.c_ulonglong)]
     L.ipeps_profile_tc_executed.argtypes = [dp]
     L.ipeps_profile_counters.argtypes = [P(ctypes.c_ulonglong), i]
+    L.ipeps_kernel_orth.argtypes = [i, i, i, vp, vp, i, vp, vp]
     L.ipeps_kernel_fp64_peak.argtypes = [dp]
     L.ipeps_kernel_svd_noalloc.argtypes = [i, i, i, vp, vp, vp, vp, d, i, vp, vp]
     L.ipeps_kernel_zgemm_split.argtypes = [i, i, i, i, i, i, vp, ll, ll, vp, ll, ll, vp, ll, ll, vp]
+    L.ipeps_kernel_zgemm_split_tf32.argtypes = [i, i, i, i, i, i, vp, ll, ll, vp, ll, ll, vp, ll, ll, vp]
     for name in EXPORTS:
         if name not in ("ipeps_last_error", "ipeps_launch_count", "ipeps_profile_name"):
             getattr(L, name).restype = ctypes.c_int
@@ -110,18 +115,18 @@ def _check(rc, handle=None, allow=()):
     return rc
 
 
-def _params(J, V, h, D, chi, order, dt, precision, seed, cut_rel=0.0, projector_svd=0):
+def _params(J, V, h, D, chi, order, dt, precision, seed, cut_rel=0.0, projector_svd=0, d_A=2):
     J = np.ascontiguousarray(np.atleast_1d(J), dtype=np.float64)
     V = np.ascontiguousarray(np.broadcast_to(np.atleast_1d(V), J.shape), dtype=np.float64)
     h = np.ascontiguousarray(np.broadcast_to(np.atleast_1d(h), J.shape), dtype=np.float64)
-    p = Params(batch=len(J), d_A=2, D=D, chi=chi, trotter_order=order, dt=dt, precision=precision,
+    p = Params(batch=len(J), d_A=d_A, D=D, chi=chi, trotter_order=order, dt=dt, precision=precision,
                seed=seed, J=_dptr(J), V=_dptr(V), h=_dptr(h), ctm_cut_rel=cut_rel,
                projector_svd=projector_svd)
     return p, (J, V, h)
 
 
-def footprint_bytes(J, V, h, D, chi, order=2, dt=0.05, precision=FP64, seed=0):
-    p, keep = _params(J, V, h, D, chi, order, dt, precision, seed)
+def footprint_bytes(J, V, h, D, chi, order=2, dt=0.05, precision=FP64, seed=0, d_A=2):
+    p, keep = _params(J, V, h, D, chi, order, dt, precision, seed, d_A=d_A)
     out = ctypes.c_size_t(0)
     _check(lib().ipeps_footprint_bytes(ctypes.byref(p), ctypes.byref(out)))
     return out.value
@@ -131,9 +136,9 @@ class IPEPS:
     """One library handle: ``batch`` = len(J) instances with shared D, chi, Trotter order and dt."""
 
     def __init__(self, J, V, h, D, chi, order=1, dt=0.02, precision=FP64, seed=0, stream=None,
-                 cut_rel=0.0, projector_svd=0):
-        p, self._keep = _params(J, V, h, D, chi, order, dt, precision, seed, cut_rel, projector_svd)
-        self.batch, self.D, self.chi, self.d = p.batch, D, chi, 4
+                 cut_rel=0.0, projector_svd=0, d_A=2):
+        p, self._keep = _params(J, V, h, D, chi, order, dt, precision, seed, cut_rel, projector_svd, d_A)
+        self.batch, self.D, self.chi, self.d = p.batch, D, chi, 2 * d_A
         self._h = ctypes.c_void_p(None)
         st = ctypes.c_void_p(stream) if stream else None
         _check(lib().ipeps_init(ctypes.byref(p), st, ctypes.byref(self._h)))
@@ -243,7 +248,7 @@ def profile_tc_executed():
 
 
 COUNTERS = ("jacobi_problems", "jacobi_rounds", "jacobi_sweeps", "subspace_rounds",
-            "subspace_accepted", "subspace_unconverged")
+            "subspace_accepted", "subspace_unconverged", "orth_fallback")
 
 
 def profile_counters():

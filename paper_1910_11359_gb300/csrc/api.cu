@@ -9,6 +9,7 @@
 #include "ctx.cuh"
 #include "measure.cuh"
 #include "model.cuh"
+#include "orth.cuh"
 #include "tc_gemm.cuh"
 
 using namespace ipeps;
@@ -58,26 +59,33 @@ ipeps_status check_dev(ipeps_h h) {
 ipeps_status validate(const ipeps_params* p, std::string* why) {
   if (!p) { *why = "params is NULL"; return IPEPS_EINVAL; }
   if (p->batch < 1 || p->batch > 4096) { *why = "batch must be in [1, 4096]"; return IPEPS_EINVAL; }
-  if (p->d_A != 2) { *why = "only d_A = 2 is implemented"; return IPEPS_EUNSUPPORTED; }
+  if (p->d_A < 2 || p->d_A > 5) { *why = "d_A must be in [2, 5]"; return IPEPS_EINVAL; }
   if (p->D < 2 || p->D > 8) { *why = "D must be in [2, 8]"; return IPEPS_EINVAL; }
+  if (p->D * p->D < 2 * p->d_A) {
+    *why = "the reduced simple update needs D^2 >= d = 2 d_A";
+    return IPEPS_EUNSUPPORTED;
+  }
+  {
+    const int d = 2 * p->d_A, nt = d * d * p->D;
+    if (!jacobi_svd_supported(nt, nt) || !jacobi_svd_fits(p->D * p->D * p->D, d * p->D)) {
+      *why = "d^2 D too large for the simple-update SVD";
+      return IPEPS_EUNSUPPORTED;
+    }
+  }
   if (p->chi < p->D * p->D) { *why = "chi must be >= D^2"; return IPEPS_EINVAL; }
   if (p->chi > 2048) { *why = "chi above 2048 is not supported"; return IPEPS_EUNSUPPORTED; }
   if (p->trotter_order != 1 && p->trotter_order != 2) { *why = "trotter_order must be 1 or 2"; return IPEPS_EINVAL; }
   if (!(p->dt > 0.0)) { *why = "dt must be > 0"; return IPEPS_EINVAL; }
-  if (p->precision == IPEPS_SPLIT_TF32X3) {
-    *why = "IPEPS_SPLIT_TF32X3 is not implemented in this build (use IPEPS_SPLIT_BF16X3)";
-    return IPEPS_EUNSUPPORTED;
-  }
-  if (p->precision != IPEPS_FP64 && p->precision != IPEPS_SPLIT_BF16X3) {
-    *why = "precision must be IPEPS_FP64 or IPEPS_SPLIT_BF16X3";
+  if (p->precision != IPEPS_FP64 && p->precision != IPEPS_SPLIT_BF16X3 && p->precision != IPEPS_SPLIT_TF32X3) {
+    *why = "precision must be IPEPS_FP64, IPEPS_SPLIT_BF16X3 or IPEPS_SPLIT_TF32X3";
     return IPEPS_EINVAL;
   }
   if (!p->J || !p->V || !p->h) { *why = "J, V, h arrays are required"; return IPEPS_EINVAL; }
   const int N = p->chi * p->D * p->D;
-  const int k = p->chi + 8 < N ? p->chi + 8 : N;
+  const int k = subspace_size(p->chi, N);
   const bool sub = p->projector_svd == 2 ? k < N : (p->projector_svd == 1 ? false : N > 2 * k);
   if (p->projector_svd < 0 || p->projector_svd > 2) { *why = "projector_svd must be 0, 1 or 2"; return IPEPS_EINVAL; }
-  if (sub && k > 256) { *why = "chi + 8 must not exceed 256 for the subspace projector SVD"; return IPEPS_EUNSUPPORTED; }
+  if (sub && k > 256) { *why = "the projector subspace (chi + max(8, chi / 4)) must not exceed 256"; return IPEPS_EUNSUPPORTED; }
   if (sub ? !jacobi_svd_supported(N, k) : !jacobi_svd_fits(N, N)) {
     *why = "chi * D^2 too large for the projector SVD";
     return IPEPS_EUNSUPPORTED;
@@ -100,6 +108,7 @@ void carve_all(ipeps_ctx* x) {
   c.gates = a.take<cplx>((size_t)2 * B * d * d * d * d);
   c.bondop = a.take<cplx>((size_t)B * d * d * d * d);
   c.derr = a.take<unsigned>(1);
+  c.dflag = a.take<int>(1);
   SuWork& s = c.su;
   s.Amat = a.take<cplx>((size_t)B * D3 * n); s.Bmat = a.take<cplx>((size_t)B * D3 * n);
   s.UA = a.take<cplx>((size_t)B * D3 * n); s.UB = a.take<cplx>((size_t)B * D3 * n);
@@ -109,6 +118,12 @@ void carve_all(ipeps_ctx* x) {
   s.X = a.take<cplx>((size_t)B * nt * nt); s.Y = a.take<cplx>((size_t)B * nt * nt);
   s.Stheta = a.take<double>((size_t)B * nt);
   s.kept = a.take<int>(B);
+  s.tgwork = nullptr;
+  s.tgwork_bytes = 0;
+  if (!jacobi_svd_fits(nt, nt)) {
+    s.tgwork_bytes = jacobi_svd_global_bytes(nt, nt, B);
+    s.tgwork = a.take<cplx>(s.tgwork_bytes / sizeof(cplx) + 1);
+  }
   ctm_carve(c);
   measure_carve(a, x->mw, B, d, D, c.chi);
 }
@@ -153,7 +168,7 @@ void set_params(Ctx& c, const ipeps_params* p) {
   c.N = c.chi * c.D2; c.order = p->trotter_order; c.dt = p->dt; c.precision = p->precision;
   c.seed = p->seed;
   c.cut_rel = p->ctm_cut_rel > 0.0 ? p->ctm_cut_rel : 1e-10;
-  c.k = c.chi + 8 < c.N ? c.chi + 8 : c.N;
+  c.k = subspace_size(c.chi, c.N);
   c.subspace = p->projector_svd == 2 ? c.k < c.N : (p->projector_svd == 1 ? false : c.N > 2 * c.k);
 }
 
@@ -208,6 +223,13 @@ ipeps_status ipeps_init(const ipeps_params* p, void* cuda_stream, ipeps_h* out) 
     return fail(nullptr, IPEPS_ENOMEM, "cudaMalloc of the pointer tables failed");
   }
   c.pool.base = (void**)c.dev_ptrs;
+  if (cudaHostAlloc((void**)&c.hflag, sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(c.dev_ptrs);
+    cudaFree(c.dev_base);
+    delete x;
+    return fail(nullptr, IPEPS_ENOMEM, "cudaHostAlloc of the convergence flag failed");
+  }
   ipeps_h h = x;
   auto cuda = [&](cudaError_t e, const char* what) -> ipeps_status {
     if (e == cudaSuccess) return IPEPS_OK;
@@ -244,6 +266,7 @@ ipeps_status ipeps_init(const ipeps_params* p, void* cuda_stream, ipeps_h* out) 
   *out = h;
   return IPEPS_OK;
 bad:
+  cudaFreeHost(c.hflag);
   cudaFree(c.dev_ptrs);
   cudaFree(c.dev_base);
   delete x;
@@ -253,6 +276,7 @@ bad:
 ipeps_status ipeps_destroy(ipeps_h h) {
   if (!h) return IPEPS_OK;
   cudaStreamSynchronize(h->c.st);
+  cudaFreeHost(h->c.hflag);
   cudaFree(h->c.dev_ptrs);
   cudaFree(h->c.dev_base);
   delete h;
@@ -312,9 +336,11 @@ ipeps_status ctmrg_converge(ipeps_h h, double tol, int max_sweeps, int* sweeps_o
   cudaMemsetAsync(c.w.sweeps, 0, sizeof(int) * B, c.st);
   if ((rc = ctm_spectra(c, tol, 1))) return from_rc(h, rc);
   std::vector<int> frozen(B, 0);
-  // split precision: its contractions leave a noise floor near 1e-6 in the corner spectra, so a
-  // requested tolerance below 1e-7 is raised to 1e-7 (the stall rule covers the rest)
-  const double tol_eff = tol > 0.0 ? (c.precision == 1 && tol < 1e-7 ? 1e-7 : tol) : -1.0;
+  // split precision: its contractions leave a noise floor in the corner spectra (near 1e-6 for
+  // BF16x3, 1e-8 for TF32x3), so a requested tolerance below split_tol_floor is raised to it (the
+  // stall rule covers the rest)
+  const double floor_tol = split_tol_floor(c.precision);
+  const double tol_eff = tol > 0.0 ? (tol < floor_tol ? floor_tol : tol) : -1.0;
   for (int s = 0; s < max_sweeps; ++s) {
     if ((rc = ctm_sweep(c))) return from_rc(h, rc);
     if ((rc = ctm_spectra(c, tol_eff, 0))) return from_rc(h, rc);
@@ -349,17 +375,18 @@ ipeps_status ipeps_measure(ipeps_h h, ipeps_obs* out) {
   if (!h || !out) return fail(h, IPEPS_EINVAL, "NULL argument");
   Ctx& c = h->c;
   if (!c.env_valid) return fail(h, IPEPS_EINVAL, "no environment: call ctmrg_converge first");
-  std::vector<double> o((size_t)8 * c.B);
+  std::vector<double> o((size_t)kObsPerInstance * c.B);
   int rc = measure_run(c, h->mw, h->mplan, o.data());
   if (rc) return from_rc(h, rc);
   ipeps_status st = check_dev(h);
   if (st != IPEPS_OK) return st;
   for (int b = 0; b < c.B; ++b) {
     ipeps_obs& r = out[b];
-    const double* v = &o[(size_t)b * 8];
+    const double* v = &o[(size_t)b * kObsPerInstance];
     r.t = h->t_measured;
     r.nA = v[0]; r.nB = v[1]; r.imbalance = v[2]; r.tauzA = v[3]; r.tauzB = v[4];
     r.energy = v[5]; r.purityA = v[6];
+    r.renyi1A = v[8]; r.renyi_halfA = v[9]; r.renyi2A = v[10];
     r.trunc_err_acc = h->last_eps[b];
     r.ctm_sweeps = h->last_sweeps[b];
     r.ctm_delta = h->last_delta[b];
@@ -460,6 +487,38 @@ int ipeps_kernel_zgemm(int M, int N, int K, int batch, int opA, int opB, const d
   return zgemm_f64(g, (cudaStream_t)stream);
 }
 
+int ipeps_kernel_orth(int N, int k, int batch, const double* X, double* Q, int passes, int* fail_out,
+                      void* stream) {
+  if (N < k || k < 1 || batch < 1 || passes < 2 || !X || !Q) { set_thread_error("bad orth arguments"); return IPEPS_EINVAL; }
+  if (!orth_supported(k)) { set_thread_error("orth: k too large"); return IPEPS_EUNSUPPORTED; }
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t wb = orth_work_bytes(N, k, batch);
+  void* work = nullptr;
+  int* dfail = nullptr;
+  if (cudaMalloc(&work, wb) != cudaSuccess || cudaMalloc(&dfail, sizeof(int) * batch) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(work);
+    set_thread_error("cudaMalloc failed");
+    return IPEPS_ENOMEM;
+  }
+  int rc = 0;
+  if (cudaMemsetAsync(dfail, 0, sizeof(int) * batch, st) != cudaSuccess)
+    rc = cuda_fail(cudaGetLastError(), "orth fail flags", __FILE__, __LINE__);
+  OrthDesc d;
+  d.N = N; d.k = k; d.batch = batch;
+  d.X = (const cplx*)X; d.sX = (long long)N * k; d.Q = (cplx*)Q; d.sQ = (long long)N * k;
+  d.work = work; d.work_bytes = wb; d.skip = nullptr; d.fail = dfail; d.passes = passes; d.dev_fail = 1e-2;
+  if (!rc) rc = orth_cqr(d, st);
+  std::vector<int> hf(batch, 0);
+  if (!rc && (cudaMemcpyAsync(hf.data(), dfail, sizeof(int) * batch, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+              cudaStreamSynchronize(st) != cudaSuccess))
+    rc = cuda_fail(cudaGetLastError(), "orth sync", __FILE__, __LINE__);
+  cudaFree(work);
+  cudaFree(dfail);
+  if (!rc && fail_out) memcpy(fail_out, hf.data(), sizeof(int) * batch);
+  return rc;
+}
+
 int ipeps_kernel_gate(double J, double V, double h, double delta, double* out) {
   if (!out) { set_thread_error("out is NULL"); return IPEPS_EINVAL; }
   double* dbuf = nullptr;
@@ -480,9 +539,9 @@ int ipeps_kernel_gate(double J, double V, double h, double delta, double* out) {
   return rc;
 }
 
-int ipeps_kernel_zgemm_split(int M, int N, int K, int batch, int opA, int opB, const double* A,
-                             long long lda, long long sA, const double* B, long long ldb, long long sB,
-                             double* C, long long ldc, long long sC, void* stream) {
+static int split_hook(int op, int M, int N, int K, int batch, int opA, int opB, const double* A,
+                      long long lda, long long sA, const double* B, long long ldb, long long sB,
+                      double* C, long long ldc, long long sC, void* stream) {
   GemmDesc g;
   memset(&g, 0, sizeof(g));
   g.M = M; g.N = N; g.K = K; g.batch = batch; g.opA = opA; g.opB = opB;
@@ -490,7 +549,7 @@ int ipeps_kernel_zgemm_split(int M, int N, int K, int batch, int opA, int opB, c
   g.B = (const cplx*)B; g.ldb = ldb; g.sB = sB;
   g.C = (cplx*)C; g.ldc = ldc; g.sC = sC;
   g.alpha = cmk(1.0, 0.0); g.beta = cmk(0.0, 0.0);
-  const size_t bytes = tc::split_workspace_bytes(M, N, K, batch);
+  const size_t bytes = tc::split_workspace_bytes(M, N, K, batch, op);
   void* work = nullptr;
   unsigned* derr = nullptr;
   if (cudaMalloc(&work, bytes) != cudaSuccess || cudaMalloc(&derr, sizeof(unsigned)) != cudaSuccess) {
@@ -501,7 +560,7 @@ int ipeps_kernel_zgemm_split(int M, int N, int K, int batch, int opA, int opB, c
   }
   cudaStream_t st = (cudaStream_t)stream;
   cudaMemsetAsync(derr, 0, sizeof(unsigned), st);
-  int rc = tc::zgemm_split_bf16(g, work, bytes, derr, st);
+  int rc = tc::zgemm_split(g, op, work, bytes, derr, st);
   unsigned e = 0;
   if (!rc) {
     if (cudaMemcpyAsync(&e, derr, sizeof(unsigned), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -513,6 +572,18 @@ int ipeps_kernel_zgemm_split(int M, int N, int K, int batch, int opA, int opB, c
   if (rc) return rc;
   if (e & DEV_TIMEOUT) { set_thread_error("tensor-core GEMM wait timed out"); return IPEPS_ETIMEOUT; }
   return 0;
+}
+
+int ipeps_kernel_zgemm_split(int M, int N, int K, int batch, int opA, int opB, const double* A,
+                             long long lda, long long sA, const double* B, long long ldb, long long sB,
+                             double* C, long long ldc, long long sC, void* stream) {
+  return split_hook(tc::SPLIT_BF16, M, N, K, batch, opA, opB, A, lda, sA, B, ldb, sB, C, ldc, sC, stream);
+}
+
+int ipeps_kernel_zgemm_split_tf32(int M, int N, int K, int batch, int opA, int opB, const double* A,
+                                  long long lda, long long sA, const double* B, long long ldb, long long sB,
+                                  double* C, long long ldc, long long sC, void* stream) {
+  return split_hook(tc::SPLIT_TF32, M, N, K, batch, opA, opB, A, lda, sA, B, ldb, sB, C, ldc, sC, stream);
 }
 
 int ipeps_kernel_permute(const double* in, double* out, int rank, const int* dims, const int* perm,

@@ -27,10 +27,13 @@
 
 #include "ctx.cuh"
 #include "model.cuh"
+#include "orth.cuh"
 #include "prof.cuh"
 #include "tc_gemm.cuh"
 
 namespace ipeps {
+
+constexpr int kOrthMinRows = 400;   // subspace blocks of at least this many rows use Cholesky QR
 
 static inline int rot_pos(int pos, int f) {   // physical position of logical position `pos` in frame f
   return (f & 1) ? pos_of(pos >> 1, pos & 1) : pos;
@@ -95,13 +98,30 @@ void ctm_carve(Ctx& c) {
   w.sub_done = a.take<int>((size_t)2 * B);
   w.sub_rounds = a.take<int>((size_t)2 * B);
   w.sub_res = a.take<double>((size_t)2 * B);
+  // Cholesky QR pays off for tall blocks: its k x k factorisations are a fixed chain of ~2k
+  // dependent steps, while the tall Jacobi's cost per round grows with N (measured: D = 3,
+  // N = 162, tall Jacobi faster; D >= 4, N >= 512, Cholesky QR 1.4-1.6x faster per sweep)
+  c.orth = c.subspace && c.N >= kOrthMinRows && orth_supported(c.k) && jacobi_svd_fits(c.k, c.k);
+  w.orth_work = nullptr; w.orth_bytes = 0;
+  w.Uq = w.Bk = w.Xk = w.part = nullptr;
+  w.ofail = a.take<int>((size_t)2 * B);
+  w.skip_new = a.take<int>((size_t)2 * B);
+  w.skip_old = a.take<int>((size_t)2 * B);
+  if (c.orth) {
+    w.orth_bytes = orth_work_bytes(c.N, c.k, 2 * B);
+    w.orth_work = a.take<unsigned char>(w.orth_bytes);
+    w.Uq = a.take<cplx>((size_t)2 * B * Nk);
+    w.Bk = a.take<cplx>((size_t)2 * B * kk);
+    w.Xk = a.take<cplx>((size_t)2 * B * kk);
+    w.part = a.take<cplx>((size_t)2 * B * ((c.N + 63) / 64) * kk);
+  }
   w.jgwork = nullptr;
   w.jgwork_bytes = 0;
   if (c.subspace && !jacobi_svd_fits(c.N, c.k)) {
     w.jgwork_bytes = jacobi_svd_global_bytes(c.N, c.k, 2 * B);
     w.jgwork = a.take<cplx>(w.jgwork_bytes / sizeof(cplx));
   }
-  if (c.precision == 1) {
+  if (c.precision != 0) {
     // largest split product of a left move: corner GEMM 3 / edge GEMM (chi^2 x D2^2 x D2^2, 8B),
     // halves (N^3, 4B), M (N^3, 2B), projectors (N chi N, 2B), edge absorption (chi D2chi N, 2B)
     const int D2 = c.D2, chi = c.chi, N = c.N;
@@ -111,7 +131,8 @@ void ctm_carve(Ctx& c) {
                                    {chi, N, N, 2 * B}, {chi, (long long)D2 * chi, N, 2 * B},
                                    {(long long)chi * D2, (long long)D2 * chi, chi, 8 * B}};
     for (auto& sh : shapes) {
-      const size_t b = tc::split_workspace_bytes((int)sh[0], (int)sh[1], (int)sh[2], (int)sh[3]);
+      const size_t b = tc::split_workspace_bytes((int)sh[0], (int)sh[1], (int)sh[2], (int)sh[3],
+                                                 c.precision == 2 ? tc::SPLIT_TF32 : tc::SPLIT_BF16);
       mx = b > mx ? b : mx;
     }
     c.tcwork_bytes = mx;
@@ -212,6 +233,12 @@ void ctm_build_plans(Ctx& c) {
   }
   c.off.yA = pool.add(yA); c.off.yU = pool.add(yU); c.off.yS = pool.add(yS); c.off.yV = pool.add(yV);
   c.off.zA = pool.add(zA); c.off.zU = pool.add(zU); c.off.zS = pool.add(zS);
+  std::vector<const void*> bA, bU;
+  for (int q = 0; q < 2 * B; ++q) {
+    bA.push_back(w.Bk ? w.Bk + (size_t)q * kk : nullptr);
+    bU.push_back(w.Xk ? w.Xk + (size_t)q * kk : nullptr);
+  }
+  c.off.bA = pool.add(bA); c.off.bU = pool.add(bU);
 }
 
 void ctm_resolve_plans(Ctx& c) {
@@ -247,6 +274,7 @@ void ctm_resolve_plans(Ctx& c) {
   c.w.yS = P.dev<double* const*>(c.off.yS); c.w.yV = P.dev<cplx* const*>(c.off.yV);
   c.w.zA = P.dev<const cplx* const*>(c.off.zA); c.w.zU = P.dev<cplx* const*>(c.off.zU);
   c.w.zS = P.dev<double* const*>(c.off.zS);
+  c.w.bA = P.dev<const cplx* const*>(c.off.bA); c.w.bU = P.dev<cplx* const*>(c.off.bU);
 }
 
 // ----------------------------------------------------------------------------- small kernels
@@ -317,10 +345,11 @@ constexpr double kDegenRtol = 1e-10, kDegenAbs = 1e-11, kTinyRel = 1e-14;
 __global__ void proj_prep_kernel(const double* S, long long s_stride, int ns, const cplx* U,
                                  const cplx* V, int N, int chi, long long ldu, long long stride_uv,
                                  cplx* Us, cplx* Vs, int* kept, double degen_rtol, double degen_abs,
-                                 double tiny_rel, double cut_rel, const int* done = nullptr,
-                                 unsigned long long* ctr = nullptr) {
+                                 double tiny_rel, double cut_rel, const int* frozen, int B,
+                                 const int* done = nullptr, unsigned long long* ctr = nullptr) {
   // S: ns singular values (descending) per problem; U, V: N x (>= chi) with leading dimension ldu
   const int q = blockIdx.x;
+  if (skipped(frozen, B, q)) return;
   const double* s = S + (size_t)q * s_stride;
   __shared__ int sK;
   if (threadIdx.x == 0) {
@@ -399,9 +428,12 @@ __device__ __forceinline__ double rand_unit(unsigned long long seed, unsigned lo
 // tiny * sv[0] are refilled with random columns so the block keeps full rank.
 __global__ void sub_fill_kernel(const cplx* src, const double* sv, int N, int k, int random_all,
                                 unsigned long long seed, unsigned long long stream, cplx* dst,
-                                const int* skip = nullptr) {
+                                const int* skip = nullptr, int B = 1) {
   const int q = blockIdx.x;
   if (skip && skip[q]) return;
+  // the draws depend on the cut (q / B) and the element only, never on the instance's place in
+  // the batch, so an instance gets the same random columns alone and in any batch
+  const unsigned long long cut = (unsigned long long)(q / B);
   const cplx* sq = src ? src + (size_t)q * N * k : nullptr;
   const double* s = sv ? sv + (size_t)q * k : nullptr;
   cplx* dq = dst + (size_t)q * N * k;
@@ -409,7 +441,7 @@ __global__ void sub_fill_kernel(const cplx* src, const double* sv, int N, int k,
     const int j = idx % k;
     const bool fresh = random_all || (s && !(s[j] > 1e-300 && s[j] > 1e-15 * s[0]));
     if (fresh) {
-      const unsigned long long id = ((unsigned long long)q * N * k + idx) * 2;
+      const unsigned long long id = (cut * N * k + idx) * 2;
       dq[idx] = cmk(rand_unit(seed, stream, id), rand_unit(seed, stream, id + 1));
     } else {
       dq[idx] = sq[idx];
@@ -447,12 +479,12 @@ __global__ void normalize_store_kernel(const cplx* C1n, const cplx* T4n, const c
 // environment no longer updated) once delta < tol, or once delta has stalled at its rounding floor:
 // no factor-2 improvement of the best delta for kStallWindow sweeps while that best and the current
 // delta are below stall_max and the current delta is within kStallGrowth of the best
-// ("sufficiently well converged", Appendix): kStallMax on the FP64 path, kStallMaxSplit on the
-// split path, whose contractions leave a noise floor near 1e-6.  A delta that grows again after
+// ("sufficiently well converged", Appendix): stall_threshold(precision), 1e-7 on the FP64 path and
+// higher on the split paths, whose contractions leave a noise floor.  A delta that grows again after
 // coming close to a fixed point means the environment is leaving an unstable fixed point; the
 // instance keeps sweeping.  tol <= 0 never freezes.
 constexpr int kStallWindow = 10;
-constexpr double kStallMax = 1e-7, kStallMaxSplit = 1e-5, kStallGrowth = 4.0;
+constexpr double kStallGrowth = 4.0;
 
 __global__ void spectra_delta_kernel(const double* cs, double* prev, int B, int chi, int first,
                                      double tol, double stall_max, double* delta, int* frozen, int* sweeps,
@@ -527,8 +559,9 @@ int ctm_init_env(Ctx& c) {
 constexpr double kSplitMinWork = 1 << 18;
 
 static int contract(Ctx& c, const GemmDesc& g) {
-  if (c.precision == 1 && (double)g.M * g.N * (double)g.K >= kSplitMinWork && !g.skip)
-    return tc::zgemm_split_bf16(g, c.tcwork, c.tcwork_bytes, c.derr, c.st);
+  if (c.precision != 0 && (double)g.M * g.N * (double)g.K >= kSplitMinWork)
+    return tc::zgemm_split(g, c.precision == 2 ? tc::SPLIT_TF32 : tc::SPLIT_BF16, c.tcwork, c.tcwork_bytes,
+                           c.derr, c.st);
   return zgemm_f64(g, c.st);
 }
 
@@ -541,12 +574,31 @@ static GemmDesc gd(int M, int N, int K, int batch) {
   return g;
 }
 
+// A product of a directional move, one problem per (slot, instance) with the instance index
+// b = problem % B: instances whose environment has converged (frozen) are skipped.
+static GemmDesc gdm(const Ctx& c, int M, int N, int K, int batch) {
+  GemmDesc g = gd(M, N, K, batch);
+  g.skip = c.w.frozen;
+  g.skip_mod = c.B;
+  return g;
+}
+
+// subspace problems q < 2B start "done" when their instance has converged
+__global__ void sub_init_kernel(int* done, int* rounds, const int* frozen, int B) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < 2 * B) {
+    done[q] = frozen[q % B] ? 1 : 0;
+    rounds[q] = 0;
+  }
+}
+
 // Columns of Z = M^+ U_y with negligible norm (M has rank below k, or u_j is a zero column) are
 // replaced by random columns before Z is orthonormalised, so the block keeps full rank.
 __global__ void sub_refill_kernel(cplx* Z, int N, int k, unsigned long long seed,
-                                  unsigned long long stream, const int* skip) {
+                                  unsigned long long stream, const int* skip, int B) {
   const int q = blockIdx.x;
   if (skip[q]) return;
+  const unsigned long long cut = (unsigned long long)(q / B);   // batch-independent draws
   cplx* Zq = Z + (size_t)q * N * k;
   __shared__ double nrm[256];
   __shared__ double mx;
@@ -565,7 +617,7 @@ __global__ void sub_refill_kernel(cplx* Z, int N, int k, unsigned long long seed
   for (int idx = threadIdx.x; idx < N * k; idx += blockDim.x) {
     const int j = idx % k;
     if (!(nrm[j] > 1e-300 && nrm[j] > 1e-13 * mx)) {
-      const unsigned long long id = ((unsigned long long)q * N * k + idx) * 2;
+      const unsigned long long id = (cut * N * k + idx) * 2;
       Zq[idx] = cmk(rand_unit(seed, stream, id), rand_unit(seed, stream, id + 1));
     }
   }
@@ -573,7 +625,9 @@ __global__ void sub_refill_kernel(cplx* Z, int N, int k, unsigned long long seed
 
 // Convergence of the subspace iteration: with Y = M V = U_y S_y W^+ and V_f = V W (so that
 // M v_j = s_j u_j holds by construction), the triplets are converged when M^+ u_j = s_j v_j too:
-// residual_j = || (M^+ U_y)_j - s_j (V_f)_j || <= rtol * s_1 for the first min(k, chi + 1) columns.
+// residual_j = || (M^+ U_y)_j - s_j (V_f)_j || <= rtol * s_1 for the first min(k, chi + 1) columns
+// (rtol = 1e-14, near the accuracy of a dense FP64 SVD: the projectors then stay within rounding
+// of the exact ones, to which the readouts and corner spectra are compared).
 __global__ void sub_residual_kernel(const cplx* Z, const cplx* Vf, const double* S, int N, int k,
                                     int ncheck, double rtol, double stag, int* done, int* rounds,
                                     double* prev, unsigned long long* ctr) {
@@ -601,9 +655,10 @@ __global__ void sub_residual_kernel(const cplx* Z, const cplx* Vf, const double*
   }
   if (threadIdx.x == 0) {
     const double r = sqrt(worst);
-    // accepted at rtol, or once the residual stops shrinking (factor 2 per round) below stag s_1:
-    // then it sits at the rounding floor of the small directions
-    if (r <= rtol * s[0] || (rounds[q] > 0 && r <= stag * s[0] && r > 0.5 * prev[q])) {
+    // accepted at rtol, or once the residual has stopped shrinking (less than 10% per round) below
+    // stag s_1: then it sits at the rounding floor of the small directions (slow convergence above
+    // that level is not a floor and goes on iterating)
+    if (r <= rtol * s[0] || (rounds[q] > 0 && r <= stag * s[0] && r >= 0.9 * prev[q])) {
       done[q] = 1;
       if (ctr) atomicAdd(ctr + CTR_SUB_ACCEPTED, 1ull);
     }
@@ -613,13 +668,54 @@ __global__ void sub_residual_kernel(const cplx* Z, const cplx* Vf, const double*
   }
 }
 
-// Top-k SVD of M = R R~ (k = chi + 8 < N/2) by block subspace iteration with Jacobi
-// orthonormalisation.  Each round: Y = M V = U_y S_y W^+ (Jacobi), V_f = V W, Z = M^+ U_y; the
-// triplets (U_y, S_y, V_f) are accepted once Z matches V_f S_y (residual test above); otherwise
-// Z (negligible columns refilled at random) = V_z S_z X^+ (Jacobi), V <- V_z (orthonormal) and the
-// next round follows.  Converged problems are skipped by
-// every later launch.  The iteration starts from the slot's previous right vectors (random on the
-// slot's first use); at most 8 rounds per call (40 on first use) -- the outer CTMRG loop calls again.
+// Per-problem path flags after a Cholesky-QR orthonormalisation: problems whose factorisation
+// broke down (fail) go to the tall Jacobi SVD (skip_old == 0), the others stay on the Cholesky-QR
+// path (skip_new == 0); converged problems take neither.
+__global__ void orth_route_kernel(const int* done, const int* fail, int* skip_new, int* skip_old, int n,
+                                  unsigned long long* ctr) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  const bool dn = done[q] != 0, fl = fail[q] != 0;
+  skip_new[q] = dn || fl;
+  skip_old[q] = dn || !fl;
+  if (!dn && fl && ctr) atomicAdd(ctr + CTR_ORTH_FALLBACK, 1ull);
+}
+
+// flag = 1 when every subspace problem has converged (or is skipped)
+__global__ void sub_all_done_kernel(const int* done, int n, int* flag) {
+  __shared__ int any_open;
+  if (threadIdx.x == 0) any_open = 0;
+  __syncthreads();
+  for (int q = threadIdx.x; q < n; q += blockDim.x)
+    if (!done[q]) any_open = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) *flag = any_open ? 0 : 1;
+}
+
+// rounds after which the host reads back whether every problem has converged (a readback is a
+// stream synchronisation, so they are spaced out geometrically)
+static bool sub_checkpoint(int rounds_done) {
+  const int marks[] = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48};
+  for (int m : marks)
+    if (rounds_done == m) return true;
+  return false;
+}
+
+// Top-k SVD of M = R R~ (k = subspace_size(chi, N) < N/2) by block subspace iteration.  Each round: Y = M V,
+// Y = U_y S_y W^+ (see below), V_f = V W (so that M v_j = s_j u_j holds by construction),
+// Z = M^+ U_y; the triplets (U_y, S_y, V_f) are accepted once Z matches V_f S_y (residual test
+// above); otherwise Z (negligible columns refilled at random) is orthonormalised into the next V.
+// The SVD of the N x k block Y and the orthonormalisation of Z are done in one of two ways:
+//  * Cholesky QR (c.orth: blocks of at least kOrthMinRows rows whose k x k factors fit): Y = U B
+//    with U from column-scaled Cholesky QR
+//    (orth.cu) and B = U^+ Y; the one-sided Jacobi SVD then runs on the k x k matrix
+//    B = X S_y W^+ only, and U_y = U X; Z is orthonormalised by Cholesky QR alone.  A problem whose
+//    factorisation breaks down (a start block far from orthonormal after column scaling) takes the
+//    tall Jacobi SVD of that round instead.
+//  * otherwise the one-sided Jacobi SVD of the N x k blocks themselves.
+// Converged problems are skipped by every later launch.  The iteration starts from the slot's
+// previous right vectors (random on the slot's first use); at most 40 rounds per call (60 on first
+// use; converged problems make the later rounds' launches exit at once).
 static int subspace_svd(Ctx& c, int f, int x, const cplx* R, const cplx* Rt) {
   CtmWork& w = c.w;
   const int B = c.B, N = c.N, k = c.k, chi = c.chi;
@@ -629,28 +725,52 @@ static int subspace_svd(Ctx& c, int f, int x, const cplx* R, const cplx* Rt) {
   cplx* slot = w.Vfin + (size_t)(f * 2 + x) * 2 * B * Nk;
   const bool warm = c.slot_warm[f][x];
   const unsigned long long stream_id = (unsigned long long)(f * 2 + x);
-  IPEPS_CUDA_TRY(cudaMemsetAsync(w.sub_done, 0, sizeof(int) * 2 * B, st));
-  IPEPS_CUDA_TRY(cudaMemsetAsync(w.sub_rounds, 0, sizeof(int) * 2 * B, st));
+  IPEPS_LAUNCH(K_PROJ_PREP, 0, st, sub_init_kernel<<<(2 * B + 127) / 128, 128, 0, st>>>(w.sub_done, w.sub_rounds,
+                                                                                     w.frozen, B));
   IPEPS_LAUNCH(K_PROJ_PREP, 0, st,
                sub_fill_kernel<<<2 * B, 256, 0, st>>>(slot, nullptr, N, k, warm ? 0 : 1, c.seed,
-                                                      stream_id, w.Vw));
-  const int rounds = warm ? 8 : 40;
+                                                      stream_id, w.Vw, w.sub_done, B));
+  const int rounds = warm ? 40 : 60;
   SvdDesc yd;
   yd.m = N; yd.n = k; yd.batch = 2 * B;
   yd.A = w.yA; yd.lda = k; yd.U = w.yU; yd.ldu = k; yd.S = w.yS; yd.V = w.yV; yd.ldv = k;
   yd.tol = 4e-16 * N; yd.max_sweeps = 60; yd.err = c.derr; yd.sweeps_out = nullptr;
-  yd.skip = w.sub_done;
+  yd.skip = c.orth ? w.skip_old : w.sub_done;
   yd.gwork = w.jgwork; yd.gwork_bytes = w.jgwork_bytes;
   SvdDesc zd = yd;
   zd.A = w.zA; zd.U = w.zU; zd.S = w.zS; zd.V = nullptr;
+  SvdDesc bd = yd;                                // k x k Jacobi of B = U^+ Y
+  bd.m = k; bd.n = k; bd.A = w.bA; bd.lda = k; bd.U = w.bU; bd.ldu = k;
+  bd.tol = 4e-16 * k; bd.skip = w.skip_new; bd.gwork = nullptr; bd.gwork_bytes = 0;
+  OrthDesc od;
+  od.N = N; od.k = k; od.batch = 2 * B; od.work = w.orth_work; od.work_bytes = w.orth_bytes;
+  od.skip = w.sub_done; od.fail = w.ofail; od.passes = 3; od.dev_fail = 1e-2;
   const int ncheck = chi + 1 < k ? chi + 1 : k;
-  const double rtol = 1e-12, stag = 1e-10;
+  const double rtol = 1e-14, stag = 1e-12;
+  auto route = [&]() -> int {
+    IPEPS_LAUNCH(K_ORTH, 0, st,
+                 orth_route_kernel<<<(2 * B + 127) / 128, 128, 0, st>>>(w.sub_done, w.ofail, w.skip_new, w.skip_old,
+                                                                       2 * B, prof_device_counters()));
+    IPEPS_CUDA_TRY(cudaGetLastError());
+    return 0;
+  };
   for (int it = 0; it < rounds; ++it) {
     GemmDesc g = gd(N, k, N, 2 * B);            // Y = M V
     g.A = w.M; g.sA = N2; g.lda = N; g.B = w.Vw; g.sB = Nk; g.ldb = k;
     g.C = w.Ysub; g.sC = Nk; g.ldc = k; g.skip = w.sub_done;
     if ((rc = zgemm_f64(g, st))) return rc;
-    if ((rc = jacobi_svd(yd, st))) return rc;
+    if (c.orth) {
+      IPEPS_CUDA_TRY(cudaMemsetAsync(w.ofail, 0, sizeof(int) * 2 * B, st));
+      od.X = w.Ysub; od.sX = Nk; od.Q = w.Uq; od.sQ = Nk;
+      if ((rc = orth_cqr(od, st)) || (rc = route())) return rc;
+      if ((rc = atb_product(w.Uq, Nk, w.Ysub, Nk, N, k, 2 * B, w.part, w.Bk, kk, w.skip_new, st))) return rc;
+      if ((rc = jacobi_svd(bd, st))) return rc;
+      g = gd(N, k, k, 2 * B);                   // U_y = U X
+      g.A = w.Uq; g.sA = Nk; g.lda = k; g.B = w.Xk; g.sB = kk; g.ldb = k;
+      g.C = w.Uy; g.sC = Nk; g.ldc = k; g.skip = w.skip_new;
+      if ((rc = zgemm_f64(g, st))) return rc;
+    }
+    if ((rc = jacobi_svd(yd, st))) return rc;   // all problems, or the fall-back ones
     g = gd(N, k, k, 2 * B);                     // V_f = V W
     g.A = w.Vw; g.sA = Nk; g.lda = k; g.B = w.W; g.sB = kk; g.ldb = k; g.C = slot; g.sC = Nk;
     g.ldc = k; g.skip = w.sub_done;
@@ -664,19 +784,30 @@ static int subspace_svd(Ctx& c, int f, int x, const cplx* R, const cplx* Rt) {
                                                             stag, w.sub_done, w.sub_rounds, w.sub_res,
                                                             prof_device_counters()));
     if (it + 1 == rounds) break;
+    if (sub_checkpoint(it + 1)) {
+      IPEPS_LAUNCH(K_PROJ_PREP, 0, st, sub_all_done_kernel<<<1, 128, 0, st>>>(w.sub_done, 2 * B, c.dflag));
+      IPEPS_CUDA_TRY(cudaMemcpyAsync(c.hflag, c.dflag, sizeof(int), cudaMemcpyDeviceToHost, st));
+      IPEPS_CUDA_TRY(cudaStreamSynchronize(st));
+      if (*c.hflag) break;
+    }
     IPEPS_LAUNCH(K_PROJ_PREP, 0, st,
                  sub_refill_kernel<<<2 * B, 256, 0, st>>>(w.Zsub, N, k, c.seed, stream_id * 1000 + it,
-                                                          w.sub_done));
-    if ((rc = jacobi_svd(zd, st))) return rc;
+                                                          w.sub_done, B));
+    if (c.orth) {
+      IPEPS_CUDA_TRY(cudaMemsetAsync(w.ofail, 0, sizeof(int) * 2 * B, st));
+      od.X = w.Zsub; od.sX = Nk; od.Q = w.Vw; od.sQ = Nk;
+      if ((rc = orth_cqr(od, st)) || (rc = route())) return rc;
+    }
+    if ((rc = jacobi_svd(zd, st))) return rc;   // all problems, or the fall-back ones
     IPEPS_LAUNCH(K_PROJ_PREP, 0, st,
                  sub_fill_kernel<<<2 * B, 256, 0, st>>>(w.Vz, nullptr, N, k, 0, c.seed, 0, w.Vw,
-                                                        w.sub_done));
+                                                        c.orth ? w.skip_old : w.sub_done, B));
   }
   c.slot_warm[f][x] = true;
   IPEPS_LAUNCH(K_PROJ_PREP, 0, st,
                proj_prep_kernel<<<2 * B, 256, 2 * chi * sizeof(double), st>>>(w.Sy, k, k, w.Uy, slot, N, chi, k, Nk, w.Us,
                                                        w.Vs, w.kept, kDegenRtol, kDegenAbs, kTinyRel, c.cut_rel,
-                                                       w.sub_done, prof_device_counters()));
+                                                       w.frozen, B, w.sub_done, prof_device_counters()));
   return 0;
 }
 
@@ -689,32 +820,32 @@ static int left_move(Ctx& c, int f, int x) {
   cudaStream_t st = c.st;
   int rc;
   // enlarged corners (8B problems)
-  GemmDesc g = gd(chi, D2 * chi, chi, 8 * B);
+  GemmDesc g = gdm(c, chi, D2 * chi, chi, 8 * B);
   g.Aptr = m.g1A; g.Bptr = m.g1B; g.Cptr = m.g1C; g.lda = chi; g.ldb = D2 * chi; g.ldc = D2 * chi;
   if ((rc = contract(c, g))) return rc;
-  g = gd(chi * D2, D2 * chi, chi, 8 * B);
+  g = gdm(c, chi * D2, D2 * chi, chi, 8 * B);
   g.Aptr = m.g2A; g.Bptr = m.g2B; g.Cptr = m.g2C; g.lda = chi; g.ldb = D2 * chi; g.ldc = D2 * chi;
   if ((rc = contract(c, g))) return rc;
   {
     const int dims[4] = {chi, D2, D2, chi}, perm[4] = {0, 3, 2, 1};
-    if ((rc = permute_c128(w.X2, w.X2p, 4, dims, perm, 8 * B, N2, N2, st))) return rc;
+    if ((rc = permute_c128(w.X2, w.X2p, 4, dims, perm, 8 * B, N2, N2, st, w.frozen, B))) return rc;
   }
-  g = gd(chi * chi, D2 * D2, D2 * D2, 8 * B);
+  g = gdm(c, chi * chi, D2 * D2, D2 * D2, 8 * B);
   g.A = w.X2p; g.sA = N2; g.lda = D2 * D2;
   g.Bptr = m.g3B; g.ldb = D2 * D2;
   g.C = w.Y; g.sC = N2; g.ldc = D2 * D2;
   if ((rc = contract(c, g))) return rc;
   {
     const int dims[4] = {chi, chi, D2, D2}, perm[4] = {0, 2, 1, 3};
-    if ((rc = permute_c128(w.Y, w.Q, 4, dims, perm, 8 * B, N2, N2, st))) return rc;
+    if ((rc = permute_c128(w.Y, w.Q, 4, dims, perm, 8 * B, N2, N2, st, w.frozen, B))) return rc;
   }
   // halves and the product over the cut
-  g = gd(N, N, N, 4 * B);
+  g = gdm(c, N, N, N, 4 * B);
   g.Aptr = m.hA; g.Bptr = m.hB; g.Cptr = m.hC; g.lda = N; g.ldb = N; g.ldc = N;
   if ((rc = contract(c, g))) return rc;
   cplx* Rt = w.H;
   cplx* R = w.H + (size_t)2 * B * N2;
-  g = gd(N, N, N, 2 * B);
+  g = gdm(c, N, N, N, 2 * B);
   g.A = R; g.sA = N2; g.lda = N; g.B = Rt; g.sB = N2; g.ldb = N; g.C = w.M; g.sC = N2; g.ldc = N;
   if ((rc = contract(c, g))) return rc;
   if (!c.subspace) {
@@ -722,57 +853,59 @@ static int left_move(Ctx& c, int f, int x) {
     SvdDesc sd;
     sd.m = N; sd.n = N; sd.batch = 2 * B;
     sd.A = w.pA; sd.lda = N; sd.U = w.pU; sd.ldu = N; sd.S = w.pS; sd.V = w.pV; sd.ldv = N;
-    sd.tol = 4e-16 * N; sd.max_sweeps = 80; sd.err = c.derr; sd.sweeps_out = nullptr; sd.skip = nullptr;
+    sd.tol = 4e-16 * N; sd.max_sweeps = 80; sd.err = c.derr; sd.sweeps_out = nullptr;
+    sd.skip = w.frozen; sd.skip_mod = B;
     if ((rc = jacobi_svd(sd, st))) return rc;
     IPEPS_LAUNCH(K_PROJ_PREP, 0, st,
                  proj_prep_kernel<<<2 * B, 256, 2 * chi * sizeof(double), st>>>(w.S, N, N, w.U, w.V, N, chi, N, N2, w.Us,
-                                                         w.Vs, w.kept, kDegenRtol, kDegenAbs, kTinyRel, c.cut_rel));
+                                                         w.Vs, w.kept, kDegenRtol, kDegenAbs, kTinyRel, c.cut_rel,
+                                                         w.frozen, B));
   } else {
     if ((rc = subspace_svd(c, f, x, R, Rt))) return rc;
   }
   // the projectors themselves are always formed in FP64: P = R~ V S^{-1/2} recovers the small
   // singular directions through cancellation, which a split product (error ~1e-5 of |R~| |v|)
   // would swamp for s_j below ~1e-5 s_1
-  g = gd(N, chi, N, 2 * B);     // P = R~ Vs
+  g = gdm(c, N, chi, N, 2 * B);     // P = R~ Vs
   g.A = Rt; g.sA = N2; g.lda = N; g.B = w.Vs; g.sB = Nc; g.ldb = chi; g.C = w.P; g.sC = Nc; g.ldc = chi;
   if ((rc = zgemm_f64(g, st))) return rc;
-  g = gd(chi, N, N, 2 * B);     // P~ = Us^+ R
+  g = gdm(c, chi, N, N, 2 * B);     // P~ = Us^+ R
   g.opA = OP_C; g.A = w.Us; g.sA = Nc; g.lda = chi;
   g.B = R; g.sB = N2; g.ldb = N; g.C = w.Pt; g.sC = Nc; g.ldc = N;
   if ((rc = zgemm_f64(g, st))) return rc;
   // absorption: C1' = P~[y-1] (C1 T1)
-  g = gd(chi, chi, N, 2 * B);
+  g = gdm(c, chi, chi, N, 2 * B);
   g.Aptr = m.c1A; g.lda = N; g.Bptr = m.c1B; g.ldb = chi; g.C = w.C1n; g.sC = chi2; g.ldc = chi;
   if ((rc = contract(c, g))) return rc;
   // T4' = P~[y] (T4 a) P[y-1]
-  g = gd(chi * D2, D2 * chi, chi, 2 * B);
+  g = gdm(c, chi * D2, D2 * chi, chi, 2 * B);
   g.Aptr = m.z1A; g.lda = chi; g.Bptr = m.z1B; g.ldb = D2 * chi; g.C = w.Z1; g.sC = N2; g.ldc = D2 * chi;
   if ((rc = contract(c, g))) return rc;
   {
     const int dims[4] = {chi, D2, D2, chi}, perm[4] = {0, 3, 2, 1};
-    if ((rc = permute_c128(w.Z1, w.Z1p, 4, dims, perm, 2 * B, N2, N2, st))) return rc;
+    if ((rc = permute_c128(w.Z1, w.Z1p, 4, dims, perm, 2 * B, N2, N2, st, w.frozen, B))) return rc;
   }
-  g = gd(chi * chi, D2 * D2, D2 * D2, 2 * B);
+  g = gdm(c, chi * chi, D2 * D2, D2 * D2, 2 * B);
   g.A = w.Z1p; g.sA = N2; g.lda = D2 * D2; g.Bptr = m.z2B; g.ldb = D2 * D2;
   g.C = w.Z2; g.sC = N2; g.ldc = D2 * D2;
   if ((rc = contract(c, g))) return rc;
   {
     const int dims[4] = {chi, chi, D2, D2}, perm[4] = {0, 2, 3, 1};
-    if ((rc = permute_c128(w.Z2, w.Z2p, 4, dims, perm, 2 * B, N2, N2, st))) return rc;
+    if ((rc = permute_c128(w.Z2, w.Z2p, 4, dims, perm, 2 * B, N2, N2, st, w.frozen, B))) return rc;
   }
-  g = gd(chi, D2 * chi, N, 2 * B);
+  g = gdm(c, chi, D2 * chi, N, 2 * B);
   g.Aptr = m.t4A; g.lda = N; g.B = w.Z2p; g.sB = N2; g.ldb = D2 * chi; g.C = w.T4n; g.sC = T;
   g.ldc = D2 * chi;
   if ((rc = contract(c, g))) return rc;
   // C4' = (T3 C4) P[y]
-  g = gd(chi * D2, chi, chi, 2 * B);
+  g = gdm(c, chi * D2, chi, chi, 2 * B);
   g.Aptr = m.w1A; g.lda = chi; g.Bptr = m.w1B; g.ldb = chi; g.C = w.W1; g.sC = T; g.ldc = chi;
   if ((rc = contract(c, g))) return rc;
   {
     const int dims[3] = {chi, D2, chi}, perm[3] = {0, 2, 1};
-    if ((rc = permute_c128(w.W1, w.W1p, 3, dims, perm, 2 * B, T, T, st))) return rc;
+    if ((rc = permute_c128(w.W1, w.W1p, 3, dims, perm, 2 * B, T, T, st, w.frozen, B))) return rc;
   }
-  g = gd(chi, chi, N, 2 * B);
+  g = gdm(c, chi, chi, N, 2 * B);
   g.A = w.W1p; g.sA = T; g.lda = N; g.Bptr = m.c4B; g.ldb = chi; g.C = w.C4n; g.sC = chi2; g.ldc = chi;
   if ((rc = contract(c, g))) return rc;
   IPEPS_LAUNCH(K_NORM_STORE, 0, st,
@@ -793,11 +926,12 @@ int ctm_spectra(Ctx& c, double tol, int first) {
   SvdDesc sd;
   sd.m = c.chi; sd.n = c.chi; sd.batch = 16 * c.B;
   sd.A = c.w.csA; sd.lda = c.chi; sd.U = nullptr; sd.ldu = 0; sd.S = c.w.csS; sd.V = nullptr; sd.ldv = 0;
-  sd.tol = 4e-16 * c.chi; sd.max_sweeps = 80; sd.err = c.derr; sd.sweeps_out = nullptr; sd.skip = nullptr;
+  sd.tol = 4e-16 * c.chi; sd.max_sweeps = 80; sd.err = c.derr; sd.sweeps_out = nullptr;
+  sd.skip = c.w.frozen; sd.skip_mod = c.B;
   if (int rc = jacobi_svd(sd, c.st)) return rc;
   IPEPS_LAUNCH(K_SPECTRA, 0, c.st,
                spectra_delta_kernel<<<c.B, 32, 0, c.st>>>(c.w.cs, c.w.prev, c.B, c.chi, first, tol,
-                                                          c.precision == 1 ? kStallMaxSplit : kStallMax, c.w.delta,
+                                                          stall_threshold(c.precision), c.w.delta,
                                                           c.w.frozen, c.w.sweeps, c.w.best, c.w.since));
   IPEPS_CUDA_TRY(cudaGetLastError());
   return 0;

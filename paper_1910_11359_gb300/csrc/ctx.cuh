@@ -34,7 +34,7 @@ struct MoveOff {
 };
 struct CtmOff {
   MoveOff mv[4][2];
-  size_t csA, csS, pA, pU, pS, pV, envC, envT, yA, yU, yS, yV, zA, zU, zS;
+  size_t csA, csS, pA, pU, pS, pV, envC, envT, yA, yU, yS, yV, zA, zU, zS, bA, bU;
 };
 
 struct CtmWork {
@@ -71,13 +71,22 @@ struct CtmWork {
   size_t jgwork_bytes;
   const cplx* const* yA; cplx* const* yU; double* const* yS; cplx* const* yV;   // Jacobi of Y
   const cplx* const* zA; cplx* const* zU; double* const* zS;                    // Jacobi of Z
+  // Cholesky-QR subspace rounds (used when the k x k blocks fit; see subspace_svd)
+  void* orth_work; size_t orth_bytes;
+  cplx* Uq;                          // [2B][N k] orthonormal basis of Y
+  cplx* Bk;                          // [2B][k k] Uq^+ Y
+  cplx* Xk;                          // [2B][k k] left singular vectors of Bk
+  cplx* part;                        // split-K partial products of Uq^+ Y
+  int *ofail, *skip_new, *skip_old;  // [2B] per-problem path flags
+  const cplx* const* bA; cplx* const* bU;                                        // Jacobi of Bk
 };
 
 struct Ctx {
   // parameters
   int B = 1, dA = 2, d = 4, D = 2, D2 = 4, chi = 8, N = 32, order = 1, precision = 0;
-  int k = 32;              // projector subspace size (min(N, chi + 8))
+  int k = 32;              // projector subspace size (subspace_size)
   bool subspace = false;   // top-k subspace iteration instead of the full Jacobi SVD of M
+  bool orth = false;       // subspace rounds by Cholesky QR + k x k Jacobi (else tall Jacobi)
   bool slot_warm[4][2] = {{false, false}, {false, false}, {false, false}, {false, false}};
   double dt = 0.02;
   double cut_rel = 1e-10;  // CTMRG projector truncation (relative)
@@ -111,6 +120,8 @@ struct Ctx {
   bool env_valid = false;
   double t = 0.0;
   unsigned* derr = nullptr;
+  int* dflag = nullptr;                   // device scratch flag (all subspace problems converged)
+  int* hflag = nullptr;                   // pinned host copy of dflag
   std::string msg;
 
   long long N2() const { return (long long)N * N; }
@@ -126,6 +137,20 @@ int ctm_prepare_tensors(Ctx& c);          // physical tensors + double layers fr
 int ctm_init_env(Ctx& c);                 // traced double-layer start, zero-padded to chi
 int ctm_sweep(Ctx& c);                    // one sweep: left, top, right, bottom moves
 int ctm_spectra(Ctx& c, double tol, int first);   // corner spectra, delta, freeze converged
+
+// Size of the projector subspace: chi + max(8, chi / 4) oversampling columns (at most N).  The
+// top chi + 1 triplets converge at the rate (s_(k+1) / s_(chi+1))^2 per round, so the oversampling
+// grows with chi, where spectra are flatter around the cut.
+inline int subspace_size(int chi, int N) {
+  const int over = chi / 4 > 8 ? chi / 4 : 8;
+  return chi + over < N ? chi + over : N;
+}
+
+// Split-precision noise floors of the CTMRG convergence test: the smallest tolerance a split path
+// honours (a smaller request is raised to it) and the stall threshold (a change that stops
+// improving below it counts as stalled).  FP64: none and 1e-7.
+inline double split_tol_floor(int precision) { return precision == 1 ? 1e-7 : precision == 2 ? 1e-8 : 0.0; }
+inline double stall_threshold(int precision) { return precision == 1 ? 1e-5 : precision == 2 ? 1e-6 : 1e-7; }
 
 // site type (0 = A, 1 = B) at a unit-cell position
 __host__ __device__ inline int site_of(int pos) { return ((pos & 1) + (pos >> 1)) & 1; }

@@ -96,8 +96,34 @@ __global__ void rho2_kernel(const cplx* const* L1, const cplx* const* L2, int ch
   }
 }
 
+// Renyi entropies S_1, S_1/2, S_2 of the physical one-site RDM of A: the auxiliary level traced out
+// of rho_A (s = n * d_A + a), normalised; its two eigenvalues in closed form (2 x 2 Hermitian).
+__device__ void renyi_phys(const cplx* r, int d, int dA, double* S1, double* Sh, double* S2) {
+  double a = 0.0, c = 0.0;
+  cplx off = cmk(0.0, 0.0);
+  for (int x = 0; x < dA; ++x) {
+    a += r[(size_t)x * d + x].x;                           // n = 0
+    c += r[(size_t)(dA + x) * d + dA + x].x;               // n = 1
+    off = cadd(off, r[(size_t)x * d + dA + x]);            // <n=0| rho |n=1>
+  }
+  const double tr = a + c;
+  a /= tr; c /= tr;
+  const double ox = off.x / tr, oy = off.y / tr;
+  const double mid = 0.5 * (a + c), rad = sqrt(0.25 * (a - c) * (a - c) + ox * ox + oy * oy);
+  double p[2] = {fmax(mid + rad, 0.0), fmax(mid - rad, 0.0)};
+  double s1 = 0.0, sq = 0.0, p2 = 0.0;
+  for (int i = 0; i < 2; ++i) {
+    if (p[i] > 0.0) s1 -= p[i] * log(p[i]);
+    sq += sqrt(p[i]);
+    p2 += p[i] * p[i];
+  }
+  *S1 = s1;
+  *Sh = 2.0 * log(sq);
+  *S2 = -log(p2);
+}
+
 // Observables per instance from rho1 (A, B) and the four bond RDMs:
-// out[b] = {nA, nB, I, tauzA, tauzB, energy, purityA, tr_rhoA}
+// out[b] = {nA, nB, I, tauzA, tauzB, energy, purityA, tr_rhoA, S1_A, S1/2_A, S2_A}
 __global__ void observables_kernel(const cplx* rho1, const cplx* rho2, const cplx* bondop,
                                    const double* h, int B, int d, int dA, double* out) {
   const int b = blockIdx.x;
@@ -135,10 +161,11 @@ __global__ void observables_kernel(const cplx* rho1, const cplx* rho2, const cpl
   for (int s = 0; s < d; ++s)
     for (int t = 0; t < d; ++t) pur += cmul(rA[s * d + t], rA[t * d + s]).x;
   pur /= tr[0] * tr[0];
-  double* o = out + (size_t)b * 8;
+  double* o = out + (size_t)b * kObsPerInstance;
   o[0] = n[0]; o[1] = n[1]; o[2] = n[0] - n[1]; o[3] = tz[0]; o[4] = tz[1];
   o[5] = 0.5 * (eb + h[b] * (tn[0] + tn[1]));
   o[6] = pur; o[7] = tr[0];
+  renyi_phys(rA, d, dA, &o[8], &o[9], &o[10]);
 }
 
 static GemmDesc gdm(int M, int N, int K, int batch) {
@@ -170,7 +197,7 @@ void measure_carve(Arena& a, MeasureWork& w, int B, int d, int D, int chi) {
   w.RC = a.take<cplx>((size_t)2 * B * T);
   w.rho1 = a.take<cplx>((size_t)2 * B * d * d);
   w.rho2 = a.take<cplx>((size_t)4 * B * d * d * d * d);
-  w.obs = a.take<double>((size_t)8 * B);
+  w.obs = a.take<double>((size_t)kObsPerInstance * B);
 }
 
 void measure_build(Ctx& c, MeasureWork& w, PtrPool& pool, MeasureOff& o) {
@@ -277,7 +304,7 @@ int measure_run(Ctx& c, MeasureWork& w, const MeasurePlan& m, double* host_out) 
   IPEPS_CUDA_TRY(cudaGetLastError());
   IPEPS_LAUNCH(K_OBS, 0, st, observables_kernel<<<B, 32, 0, st>>>(w.rho1, w.rho2, c.bondop, c.dh, B, d, c.dA, w.obs));
   IPEPS_CUDA_TRY(cudaGetLastError());
-  IPEPS_CUDA_TRY(cudaMemcpyAsync(host_out, w.obs, sizeof(double) * 8 * B, cudaMemcpyDeviceToHost, st));
+  IPEPS_CUDA_TRY(cudaMemcpyAsync(host_out, w.obs, sizeof(double) * kObsPerInstance * B, cudaMemcpyDeviceToHost, st));
   IPEPS_CUDA_TRY(cudaStreamSynchronize(st));
   return 0;
 }

@@ -22,6 +22,8 @@ size_t measure_bytes(int B, int d, int D, int chi);
 void measure_carve(Arena& a, MeasureWork& w, int B, int d, int D, int chi);
 void measure_build(Ctx& c, MeasureWork& w, PtrPool& pool, MeasureOff& o);
 void measure_resolve(const PtrPool& P, const MeasureOff& o, MeasurePlan& m);
-// fills host_out[b * 8 + {nA, nB, I, tauzA, tauzB, energy, purityA, tr_rhoA}]
+constexpr int kObsPerInstance = 11;
+// fills host_out[b * kObsPerInstance + {nA, nB, I, tauzA, tauzB, energy, purityA, tr_rhoA,
+// S1_A, S1/2_A, S2_A}] (Renyi entropies of the physical one-site RDM of A)
 int measure_run(Ctx& c, MeasureWork& w, const MeasurePlan& m, double* host_out);
 }  // namespace ipeps

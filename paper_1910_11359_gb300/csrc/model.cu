@@ -30,91 +30,74 @@ __device__ double bond_h_elem(int row, int col, int d, int dA, double J, double 
   return v;
 }
 
-// One CTA per (instance, delta): U = exp(-i h_b delta) by scaling and squaring of the Taylor series
-// (Moler & Van Loan, "Nineteen dubious ways to compute the exponential of a matrix", method 3):
-// X = -i h_b delta / 2^s with ||X||_1 <= 1/2, exp(X) summed to order 24 by Horner's rule, then
-// squared s times.
+// The bond Hamiltonian conserves every auxiliary level, so h_b is block diagonal: for each pair of
+// levels (aA, aB) it acts on the four occupation states (nA, nB) only, and
+// exp(-i h_b delta) = direct sum over (aA, aB) of exp(-i h_(aA,aB) delta) (4 x 4 each).
+// One CTA per (instance, delta), one thread per block: U_block = exp(X), X = -i h_block delta, by
+// scaling and squaring of the Taylor series (Moler & Van Loan, "Nineteen dubious ways to compute
+// the exponential of a matrix", method 3): X / 2^s with ||X||_1 / 2^s <= 1/2, the series summed
+// to order 24 by Horner's rule, then squared s times.  Output [delta][instance][d^2][d^2], two-site
+// index sA * d + sB with s = n * d_A + a.
 __global__ void gate_kernel(const double* J, const double* V, const double* h, const double* deltas,
                             int ndelta, int d, int dA, cplx* out) {
   const int b = blockIdx.x / ndelta, g = blockIdx.x % ndelta;
   const int d2 = d * d;
-  extern __shared__ __align__(16) unsigned char gate_smem[];
-  cplx* Xs = reinterpret_cast<cplx*>(gate_smem);            // three d2 x d2 matrices
-  cplx* Es = Xs + d2 * d2;
-  cplx* Ts = Es + d2 * d2;
-  double* colsum = reinterpret_cast<double*>(Ts + d2 * d2);
-  __shared__ int s_shift;
-#define X(r, c) Xs[(r) * d2 + (c)]
-#define E(r, c) Es[(r) * d2 + (c)]
-#define T(r, c) Ts[(r) * d2 + (c)]
-  const int tid = threadIdx.x;
+  cplx* U = out + ((size_t)g * gridDim.x / ndelta + b) * d2 * d2;
+  for (int idx = threadIdx.x; idx < d2 * d2; idx += blockDim.x) U[idx] = cmk(0.0, 0.0);
+  __syncthreads();
+  const int blk = threadIdx.x;
+  if (blk >= dA * dA) return;
+  const int aA = blk / dA, aB = blk % dA;
   const double delta = deltas[g];
-  for (int idx = tid; idx < d2 * d2; idx += blockDim.x) {
-    int r = idx / d2, c = idx % d2;
-    double hv = bond_h_elem(r, c, d, dA, J[b], V[b], h[b]);
-    X(r, c) = cmk(0.0, -hv * delta);
+  int idx[4];                                    // two-site index of local state (nA, nB) = (m/2, m%2)
+  for (int m = 0; m < 4; ++m) idx[m] = ((m >> 1) * dA + aA) * d + ((m & 1) * dA + aB);
+  cplx X[16], E[16], T[16];
+  double nrm = 0.0;
+  for (int c = 0; c < 4; ++c) {
+    double col = 0.0;
+    for (int r = 0; r < 4; ++r) {
+      const double hv = bond_h_elem(idx[r], idx[c], d, dA, J[b], V[b], h[b]);
+      X[r * 4 + c] = cmk(0.0, -hv * delta);
+      col += fabs(hv * delta);
+    }
+    nrm = fmax(nrm, col);
   }
-  __syncthreads();
-  if (tid < d2) {
-    double s = 0.0;
-    for (int r = 0; r < d2; ++r) s += fabs(X(r, tid).y);
-    colsum[tid] = s;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    double nrm = 0.0;
-    for (int c = 0; c < d2; ++c) nrm = fmax(nrm, colsum[c]);
-    int s = 0;
-    while (nrm > 0.5) { nrm *= 0.5; ++s; }
-    s_shift = s;
-  }
-  __syncthreads();
+  int sh = 0;
   double scale = 1.0;
-  for (int i = 0; i < s_shift; ++i) scale *= 0.5;
-  for (int idx = tid; idx < d2 * d2; idx += blockDim.x) {
-    int r = idx / d2, c = idx % d2;
-    X(r, c) = cscale(X(r, c), scale);
-    E(r, c) = cmk(r == c ? 1.0 : 0.0, 0.0);
+  while (nrm > 0.5) { nrm *= 0.5; scale *= 0.5; ++sh; }
+  for (int e = 0; e < 16; ++e) {
+    X[e] = cscale(X[e], scale);
+    E[e] = cmk((e / 4) == (e % 4) ? 1.0 : 0.0, 0.0);
   }
-  __syncthreads();
-  // Horner: E <- I + X E / k for k = K..1
-  for (int k = 24; k >= 1; --k) {
-    for (int idx = tid; idx < d2 * d2; idx += blockDim.x) {
-      int r = idx / d2, c = idx % d2;
-      cplx acc = cmk(0.0, 0.0);
-      for (int q = 0; q < d2; ++q) cfma(acc, X(r, q), E(q, c));
-      T(r, c) = cadd(cmk(r == c ? 1.0 : 0.0, 0.0), cscale(acc, 1.0 / k));
-    }
-    __syncthreads();
-    for (int idx = tid; idx < d2 * d2; idx += blockDim.x) E(idx / d2, idx % d2) = T(idx / d2, idx % d2);
-    __syncthreads();
+  // Horner: E <- I + X E / q for q = 24 .. 1
+  for (int q = 24; q >= 1; --q) {
+    for (int r = 0; r < 4; ++r)
+      for (int c = 0; c < 4; ++c) {
+        cplx acc = cmk(0.0, 0.0);
+        for (int t = 0; t < 4; ++t) cfma(acc, X[r * 4 + t], E[t * 4 + c]);
+        T[r * 4 + c] = cadd(cmk(r == c ? 1.0 : 0.0, 0.0), cscale(acc, 1.0 / q));
+      }
+    for (int e = 0; e < 16; ++e) E[e] = T[e];
   }
-  for (int sq = 0; sq < s_shift; ++sq) {
-    for (int idx = tid; idx < d2 * d2; idx += blockDim.x) {
-      int r = idx / d2, c = idx % d2;
-      cplx acc = cmk(0.0, 0.0);
-      for (int q = 0; q < d2; ++q) cfma(acc, E(r, q), E(q, c));
-      T(r, c) = acc;
-    }
-    __syncthreads();
-    for (int idx = tid; idx < d2 * d2; idx += blockDim.x) E(idx / d2, idx % d2) = T(idx / d2, idx % d2);
-    __syncthreads();
+  for (int q = 0; q < sh; ++q) {
+    for (int r = 0; r < 4; ++r)
+      for (int c = 0; c < 4; ++c) {
+        cplx acc = cmk(0.0, 0.0);
+        for (int t = 0; t < 4; ++t) cfma(acc, E[r * 4 + t], E[t * 4 + c]);
+        T[r * 4 + c] = acc;
+      }
+    for (int e = 0; e < 16; ++e) E[e] = T[e];
   }
-  cplx* U = out + ((size_t)g * gridDim.x / ndelta + b) * d2 * d2;   // [delta][instance][d2][d2]
-  for (int idx = tid; idx < d2 * d2; idx += blockDim.x) U[idx] = E(idx / d2, idx % d2);
-#undef X
-#undef E
-#undef T
+  for (int r = 0; r < 4; ++r)
+    for (int c = 0; c < 4; ++c) U[(size_t)idx[r] * d2 + idx[c]] = E[r * 4 + c];
 }
 
 int build_gates(const double* J, const double* V, const double* h, const double* deltas, int ndelta,
                 int batch, int d, int dA, cplx* out, cudaStream_t st) {
-  const int d2 = d * d;
-  const size_t smem = (size_t)3 * d2 * d2 * sizeof(cplx) + d2 * sizeof(double);
-  if (smem > 200 * 1024) return cuda_fail(cudaErrorInvalidValue, "gate size", __FILE__, __LINE__);
-  IPEPS_CUDA_TRY(cudaFuncSetAttribute(gate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
-  IPEPS_LAUNCH(K_GATE, 0, st, gate_kernel<<<batch * ndelta, 256, smem, st>>>(J, V, h, deltas, ndelta, d, dA, out));
+  if (dA < 1 || dA * dA > 1024 || d != 2 * dA)
+    return cuda_fail(cudaErrorInvalidValue, "gate size", __FILE__, __LINE__);
+  const int threads = dA * dA < 32 ? 32 : ((dA * dA + 31) / 32) * 32;
+  IPEPS_LAUNCH(K_GATE, 0, st, gate_kernel<<<batch * ndelta, threads, 0, st>>>(J, V, h, deltas, ndelta, d, dA, out));
   IPEPS_CUDA_TRY(cudaGetLastError());
   return 0;
 }

@@ -9,7 +9,7 @@ namespace ipeps {
 enum KernelClass : int {
   K_ZGEMM = 0, K_PERMUTE, K_JACOBI, K_SU_ABSORB, K_SU_THETA, K_SU_TRUNCATE, K_SU_REBUILD, K_GATE,
   K_PHYS, K_DLAYER, K_ENV_INIT, K_PROJ_PREP, K_NORM_STORE, K_SPECTRA, K_OPEN_LAYER, K_RHO1, K_RHO2,
-  K_OBS, K_INIT_STATE, K_BONDOP, K_TC_GEMM, K_TC_PREP, K_NCLASS
+  K_OBS, K_INIT_STATE, K_BONDOP, K_TC_GEMM, K_TC_PREP, K_ORTH, K_NCLASS
 };
 
 const char* kernel_class_name(int k);
@@ -28,6 +28,8 @@ enum DevCounter : int {
   CTR_SUB_ROUNDS,            // subspace-iteration rounds evaluated, summed over projector problems
   CTR_SUB_ACCEPTED,          // projector problems whose subspace iteration met its acceptance test
   CTR_SUB_UNCONVERGED,       // projector problems handed on at the round cap without meeting it
+  CTR_ORTH_FALLBACK,         // subspace blocks orthonormalised by the tall Jacobi SVD instead of
+                             // Cholesky QR (the factorisation broke down)
   CTR_N
 };
 unsigned long long* prof_device_counters();

@@ -176,6 +176,7 @@ int su_bond_update(SuWork& w, cplx* GA, cplx* GB, double* lam, double* eps, cons
   t.m = nt; t.n = nt; t.batch = batch;
   t.A = w.tA; t.lda = nt; t.U = w.tU; t.ldu = nt; t.S = w.tS; t.V = w.tV; t.ldv = nt;
   t.tol = 4e-16 * nt; t.max_sweeps = 60; t.err = err; t.sweeps_out = nullptr; t.skip = nullptr;
+  t.gwork = w.tgwork; t.gwork_bytes = w.tgwork_bytes;
   if (int rc = jacobi_svd(t, st)) return rc;
   IPEPS_LAUNCH(K_SU_TRUNCATE, 0, st,
                su_truncate_kernel<<<batch, 32, 0, st>>>(w.Stheta, nt, D, legA, lam, eps, w.kept, 1e-10, 1e-14));

@@ -13,6 +13,8 @@ struct SuWork {
   cplx *X, *Y;                  // [B][nt][nt]
   double* Stheta;               // [B][nt]
   int* kept;                    // [B]
+  cplx* tgwork;                 // Jacobi column storage for theta when it exceeds shared memory
+  size_t tgwork_bytes;
   // device pointer arrays for the batched SVDs
   const cplx* const* qA; cplx* const* qU; double* const* qS; cplx* const* qV;   // 2B
   const cplx* const* tA; cplx* const* tU; double* const* tS; cplx* const* tV;   // B

@@ -27,17 +27,28 @@
 namespace ipeps {
 namespace tc {
 
-constexpr int BM = 128, BK = 64, STAGES = 4, THREADS = 192;
-constexpr uint32_t A_BYTES = BM * BK * 2;                  // 16 KB A tile per stage
+constexpr int BM = 128, STAGES = 4, THREADS = 192;
+constexpr int ROW_BYTES = 128;                             // one 128-byte swizzled row per K tile
+constexpr uint32_t A_BYTES = BM * ROW_BYTES;               // 16 KB A tile per stage
+// Operand type of the real GEMM: OP_BF16 (tcgen05 kind::f16 with BF16 operands) or OP_TF32
+// (kind::tf32).  A K tile is one 128-byte row per operand row: 64 BF16 or 32 TF32 values; one MMA
+// covers 32 bytes of K (16 BF16 or 8 TF32), four per tile.
+constexpr int OP_BF16 = 0, OP_TF32 = 1;
+template <int OPT> struct OpCfg {
+  static constexpr int ELEM = OPT == OP_TF32 ? 4 : 2;
+  static constexpr int BK = ROW_BYTES / ELEM;              // K elements per tile
+  static constexpr uint32_t FMT = OPT == OP_TF32 ? 2u : 1u;   // instruction-descriptor A/B format
+};
 // per output-tile width BN (128 or 256): B tile bytes, shared memory, TMEM columns
-template <int BN> struct TileCfg {
-  static constexpr uint32_t B_BYTES = BN * BK * 2;
+template <int BN, int OPT> struct TileCfg {
+  static constexpr uint32_t B_BYTES = BN * ROW_BYTES;
   static constexpr uint32_t SMEM_BYTES = STAGES * (A_BYTES + B_BYTES) + 1024 + 256;
   static constexpr uint32_t TMEM_COLS = BN;
-  // instruction descriptor, kind::f16: BF16 A and B (K-major), FP32 accumulator, M = 128, N = BN
-  static constexpr uint32_t IDESC = (1u << 4)        // D format F32
-                                    | (1u << 7)      // A format BF16
-                                    | (1u << 10)     // B format BF16
+  // instruction descriptor: A and B of the operand type (same for both, K-major), FP32
+  // accumulator, M = 128, N = BN
+  static constexpr uint32_t IDESC = (1u << 4)                  // D format F32
+                                    | (OpCfg<OPT>::FMT << 7)   // A format
+                                    | (OpCfg<OPT>::FMT << 10)  // B format
                                     | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 };
 constexpr long long SPIN_LIMIT = 1LL << 24;
@@ -89,7 +100,7 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
   d |= (uint64_t)2 << 61;                  // 128-byte swizzle
   return d;
 }
-template <int BN>
+template <int BN, int OPT>
 __global__ void __launch_bounds__(THREADS, 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                float* __restrict__ C, long long ldc, long long strideC, int ktiles, unsigned* err,
@@ -100,7 +111,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   const uint32_t raw = smem_u32(smem_raw);
   unsigned char* smem = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
   const uint32_t sA = smem_u32(smem);
-  using Cfg = TileCfg<BN>;
+  using Cfg = TileCfg<BN, OPT>;
+  constexpr int BK = OpCfg<OPT>::BK;
   const uint32_t sB = sA + STAGES * A_BYTES;
   unsigned char* tail = smem + STAGES * (A_BYTES + Cfg::B_BYTES);
   uint64_t* bars = reinterpret_cast<uint64_t*>(tail);       // full[STAGES], empty[STAGES], done
@@ -170,14 +182,22 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint64_t da = smem_desc(sA + s * A_BYTES), db = smem_desc(sB + s * Cfg::B_BYTES);
 #pragma unroll
-      for (int k = 0; k < BK / 16; ++k) {
+      for (int k = 0; k < ROW_BYTES / 32; ++k) {
         const uint32_t acc = (kt > 0 || k > 0) ? 1u : 0u;
-        const uint64_t adv = (uint64_t)((k * 32) >> 4);   // 16 BF16 = 32 bytes along K
-        asm volatile(
-            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-            "l"(da + adv), "l"(db + adv), "r"(Cfg::IDESC), "r"(acc)
-            : "memory");
+        const uint64_t adv = (uint64_t)((k * 32) >> 4);   // 32 bytes along K per MMA
+        if constexpr (OPT == OP_TF32) {
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+              "l"(da + adv), "l"(db + adv), "r"(Cfg::IDESC), "r"(acc)
+              : "memory");
+        } else {
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+              "l"(da + adv), "l"(db + adv), "r"(Cfg::IDESC), "r"(acc)
+              : "memory");
+        }
       }
       // the stage is free once these MMAs have read it
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -243,18 +263,31 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 }
 
 // ----------------------------------------------------------------------------- operand preparation
-__device__ __forceinline__ void split_bf16(double x, __nv_bfloat16* hi, __nv_bfloat16* lo) {
+// x ~ hi + lo with hi, lo in the operand type: BF16 (8 significant bits each) or TF32 (11 each).
+__device__ __forceinline__ void split_term(double x, __nv_bfloat16* hi, __nv_bfloat16* lo) {
   const __nv_bfloat16 h = __float2bfloat16_rn((float)x);
   *hi = h;
   *lo = __float2bfloat16_rn((float)(x - (double)__bfloat162float(h)));
+}
+// TF32 value of an FP32 number: round to nearest (ties to even) at mantissa bit 13 and clear the
+// 13 low bits; the tensor cores read the 19 high bits of the 32-bit word
+__device__ __forceinline__ float to_tf32(float f) {
+  unsigned u = __float_as_uint(f);
+  u += 0x0FFFu + ((u >> 13) & 1u);
+  return __uint_as_float(u & 0xFFFFE000u);
+}
+__device__ __forceinline__ void split_term(double x, float* hi, float* lo) {
+  const float h = to_tf32((float)x);
+  *hi = h;
+  *lo = to_tf32((float)(x - (double)h));
 }
 
 // The operands are prepared tile by tile: a 32 x 32 tile of op(A) (rows x K) or of op(B)^T
 // (columns x K) is read with coalesced loads along whichever index is contiguous in memory, held
 // in shared memory, and written out along K, where each complex element becomes its 12 (A) or 6 (B)
-// BF16 entries.  Grid: (K tiles, row tiles, batch), so no integer division per element.  Columns
-// c >= 6K of both operands are zeroed by the host; rows beyond 2M (A3) or N (B3) only feed output
-// entries that are never read.
+// entries of the operand type T.  Grid: (K tiles, row tiles, batch), so no integer division per
+// element.  Columns c >= 6K of both operands are zeroed by the host; rows beyond 2M (A3) or N (B3)
+// only feed output entries that are never read.
 constexpr int PT = 32;
 
 // tile[r][k] = element (row0 + r, k0 + k) of the operand seen as rows x K, stored either
@@ -277,7 +310,8 @@ __device__ __forceinline__ void load_tile(cplx (*tile)[PT + 1], const cplx* P, l
 
 // A3[b] (Mp x Kp): row r < M holds [Ar | -Ai], row M + r holds [Ai | Ar]; each 2K-wide segment
 // appears as hi, hi, lo.
-__global__ void __launch_bounds__(256) prep_a_kernel(GemmDesc g, __nv_bfloat16* A3, int Mp, int Kp) {
+template <typename T>
+__global__ void __launch_bounds__(256) prep_a_kernel(GemmDesc g, T* A3, int Mp, int Kp) {
   __shared__ cplx tile[PT][PT + 1];
   const int b = blockIdx.z, M = g.M, K = g.K;
   if (skipped(g.skip, g.skip_mod, b)) return;
@@ -292,12 +326,12 @@ __global__ void __launch_bounds__(256) prep_a_kernel(GemmDesc g, __nv_bfloat16* 
     const int r = row0 + a;
     if (r >= M) break;
     const cplx v = tile[a][threadIdx.x];
-    __nv_bfloat16 rh, rl, ih, il, mh, ml;
-    split_bf16(v.x, &rh, &rl);
-    split_bf16(v.y, &ih, &il);
-    split_bf16(-v.y, &mh, &ml);
-    __nv_bfloat16* up = A3 + ((long long)b * Mp + r) * Kp;        // row r
-    __nv_bfloat16* dn = A3 + ((long long)b * Mp + M + r) * Kp;    // row M + r
+    T rh, rl, ih, il, mh, ml;
+    split_term(v.x, &rh, &rl);
+    split_term(v.y, &ih, &il);
+    split_term(-v.y, &mh, &ml);
+    T* up = A3 + ((long long)b * Mp + r) * Kp;        // row r
+    T* dn = A3 + ((long long)b * Mp + M + r) * Kp;    // row M + r
     up[k] = rh;          up[K + k] = mh;
     up[2 * K + k] = rh;  up[3 * K + k] = mh;
     up[4 * K + k] = rl;  up[5 * K + k] = ml;
@@ -308,7 +342,8 @@ __global__ void __launch_bounds__(256) prep_a_kernel(GemmDesc g, __nv_bfloat16* 
 }
 
 // B3t[b] (Np x Kp), row j = column j of B3 = [B_hi; B_lo; B_hi] with B_big = [Br; Bi] (2K x N)
-__global__ void __launch_bounds__(256) prep_b_kernel(GemmDesc g, __nv_bfloat16* B3t, int Np, int Kp) {
+template <typename T>
+__global__ void __launch_bounds__(256) prep_b_kernel(GemmDesc g, T* B3t, int Np, int Kp) {
   __shared__ cplx tile[PT][PT + 1];
   const int b = blockIdx.z, N = g.N, K = g.K;
   if (skipped(g.skip, g.skip_mod, b)) return;
@@ -323,10 +358,10 @@ __global__ void __launch_bounds__(256) prep_b_kernel(GemmDesc g, __nv_bfloat16* 
     const int j = row0 + a;
     if (j >= N) break;
     const cplx v = tile[a][threadIdx.x];
-    __nv_bfloat16 rh, rl, ih, il;
-    split_bf16(v.x, &rh, &rl);
-    split_bf16(v.y, &ih, &il);
-    __nv_bfloat16* row = B3t + ((long long)b * Np + j) * Kp;
+    T rh, rl, ih, il;
+    split_term(v.x, &rh, &rl);
+    split_term(v.y, &ih, &il);
+    T* row = B3t + ((long long)b * Np + j) * Kp;
     row[k] = rh;          row[K + k] = ih;
     row[2 * K + k] = rl;  row[3 * K + k] = il;
     row[4 * K + k] = rh;  row[5 * K + k] = ih;
@@ -369,43 +404,52 @@ static int encoder(PFN_cuTensorMapEncodeTiled_v12000* out) {
   return 0;
 }
 
-// 3-D map over [batch][rows][Kp] BF16 with a (64 x box_rows x 1) box, 128-byte swizzle
+// 3-D map over [batch][rows][Kp] of the operand type with a (128-byte x box_rows x 1) box,
+// 128-byte swizzle
+template <int OPT>
 static int make_map(CUtensorMap* map, const void* base, int rows, int Kp, int batch, int box_rows) {
   PFN_cuTensorMapEncodeTiled_v12000 enc;
   if (int rc = encoder(&enc)) return rc;
+  constexpr int E = OpCfg<OPT>::ELEM;
   cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)batch};
-  cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)rows * Kp * 2};
-  cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1};
+  cuuint64_t strides[2] = {(cuuint64_t)Kp * E, (cuuint64_t)rows * Kp * E};
+  cuuint32_t box[3] = {(cuuint32_t)OpCfg<OPT>::BK, (cuuint32_t)box_rows, 1};
   cuuint32_t estr[3] = {1, 1, 1};
-  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides,
-                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r = enc(map, OPT == OP_TF32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
+                   const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return cuda_fail(cudaErrorInvalidValue, "cuTensorMapEncodeTiled", __FILE__, __LINE__);
   return 0;
 }
 
 static inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
-// output-tile width: 256 (twice the reuse of each A tile) when that still gives every SM a tile
-static int pick_bn(int M, int N, int batch) {
-  const long long tiles256 = (long long)(round_up(2 * M, BM) / BM) * (round_up(N, 256) / 256) * batch;
+// output-tile width: 256 (twice the reuse of each A tile) for wide products whose own tiles alone
+// fill the SMs.  The choice depends on the problem's shape only, never on the batch size, so that
+// an instance gets the same arithmetic (the same MMA shapes) alone and in any batch.
+static int pick_bn(int M, int N) {
+  const long long tiles256 = (long long)(round_up(2 * M, BM) / BM) * (round_up(N, 256) / 256);
   return (N > 128 && tiles256 >= 152) ? 256 : 128;
 }
 
-size_t split_workspace_bytes(int M, int N, int K, int batch) {
-  const size_t Mp = round_up(2 * M, BM), Np = round_up(N, 256), Kp = round_up(6 * K, BK);
-  return (Mp * Kp + Np * Kp) * 2 * batch + Mp * Np * 4 * batch + 3 * 1024;
+static int k_tile(int op) { return op == SPLIT_TF32 ? OpCfg<OP_TF32>::BK : OpCfg<OP_BF16>::BK; }
+static int elem_bytes(int op) { return op == SPLIT_TF32 ? 4 : 2; }
+
+size_t split_workspace_bytes(int M, int N, int K, int batch, int op) {
+  const size_t Mp = round_up(2 * M, BM), Np = round_up(N, 256), Kp = round_up(6 * K, k_tile(op));
+  return (Mp * Kp + Np * Kp) * elem_bytes(op) * batch + Mp * Np * 4 * batch + 3 * 1024;
 }
 
-template <int BN>
+template <int BN, int OPT>
 static int launch_tc(const CUtensorMap& mA, const CUtensorMap& mB, float* C32, int Mp, int Np, int Kp,
                      int batch, double algo_flops, unsigned* err, const int* skip, int skip_mod,
                      cudaStream_t st) {
-  using Cfg = TileCfg<BN>;
+  using Cfg = TileCfg<BN, OPT>;
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [] {
-    attr_err = cudaFuncSetAttribute(tc_gemm_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    attr_err = cudaFuncSetAttribute(tc_gemm_kernel<BN, OPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)Cfg::SMEM_BYTES);
   });
   IPEPS_CUDA_TRY(attr_err);
@@ -413,58 +457,70 @@ static int launch_tc(const CUtensorMap& mA, const CUtensorMap& mB, float* C32, i
   const double flops = 2.0 * Mp * (double)Np * Kp * batch;     // executed on the tensor pipe
   prof_add_tc_executed(flops);
   IPEPS_LAUNCH(K_TC_GEMM, algo_flops > 0.0 ? algo_flops : flops, st,
-               tc_gemm_kernel<BN><<<grid, THREADS, Cfg::SMEM_BYTES, st>>>(mA, mB, C32, Np, (long long)Mp * Np,
-                                                                        Kp / BK, err, skip, skip_mod));
+               (tc_gemm_kernel<BN, OPT><<<grid, THREADS, Cfg::SMEM_BYTES, st>>>(
+                   mA, mB, C32, Np, (long long)Mp * Np, Kp / OpCfg<OPT>::BK, err, skip, skip_mod)));
   IPEPS_CUDA_TRY(cudaGetLastError());
   return 0;
+}
+
+template <int OPT>
+static int gemm_raw(const void* A3, const void* B3t, float* C32, int Mp, int Np, int Kp, int batch, int bn,
+                    double algo_flops, unsigned* err, cudaStream_t st, const int* skip, int skip_mod) {
+  if ((bn != 128 && bn != 256) || Mp % BM || Np % bn || Kp % OpCfg<OPT>::BK || batch < 1 || batch > 65535)
+    return cuda_fail(cudaErrorInvalidValue, "tc gemm shape", __FILE__, __LINE__);
+  if (((uintptr_t)A3 & 15) || ((uintptr_t)B3t & 15) || ((uintptr_t)C32 & 15))
+    return cuda_fail(cudaErrorInvalidValue, "tc gemm alignment", __FILE__, __LINE__);
+  CUtensorMap mA, mB;
+  if (int rc = make_map<OPT>(&mA, A3, Mp, Kp, batch, BM)) return rc;
+  if (int rc = make_map<OPT>(&mB, B3t, Np, Kp, batch, bn)) return rc;
+  return bn == 256 ? launch_tc<256, OPT>(mA, mB, C32, Mp, Np, Kp, batch, algo_flops, err, skip, skip_mod, st)
+                   : launch_tc<128, OPT>(mA, mB, C32, Mp, Np, Kp, batch, algo_flops, err, skip, skip_mod, st);
 }
 
 int gemm_bf16_raw(const void* A3, const void* B3t, float* C32, int Mp, int Np, int Kp, int batch,
                   int bn, double algo_flops, unsigned* err, cudaStream_t st, const int* skip,
                   int skip_mod) {
-  if ((bn != 128 && bn != 256) || Mp % BM || Np % bn || Kp % BK || batch < 1 || batch > 65535)
-    return cuda_fail(cudaErrorInvalidValue, "tc gemm shape", __FILE__, __LINE__);
-  if (((uintptr_t)A3 & 15) || ((uintptr_t)B3t & 15) || ((uintptr_t)C32 & 15))
-    return cuda_fail(cudaErrorInvalidValue, "tc gemm alignment", __FILE__, __LINE__);
-  CUtensorMap mA, mB;
-  if (int rc = make_map(&mA, A3, Mp, Kp, batch, BM)) return rc;
-  if (int rc = make_map(&mB, B3t, Np, Kp, batch, bn)) return rc;
-  return bn == 256 ? launch_tc<256>(mA, mB, C32, Mp, Np, Kp, batch, algo_flops, err, skip, skip_mod, st)
-                   : launch_tc<128>(mA, mB, C32, Mp, Np, Kp, batch, algo_flops, err, skip, skip_mod, st);
+  return gemm_raw<OP_BF16>(A3, B3t, C32, Mp, Np, Kp, batch, bn, algo_flops, err, st, skip, skip_mod);
 }
 
-int zgemm_split_bf16(const GemmDesc& g, void* work, size_t work_bytes, unsigned* err, cudaStream_t st) {
-  if (g.M <= 0 || g.N <= 0 || g.K <= 0 || g.batch <= 0) return 0;
-  const int bn = pick_bn(g.M, g.N, g.batch);
-  const int Mp = round_up(2 * g.M, BM), Np = round_up(g.N, bn), Kp = round_up(6 * g.K, BK);
-  if (split_workspace_bytes(g.M, g.N, g.K, g.batch) > work_bytes)
+template <typename T, int OPT>
+static int zgemm_split_t(const GemmDesc& g, void* work, size_t work_bytes, unsigned* err, cudaStream_t st) {
+  const int op = OPT == OP_TF32 ? SPLIT_TF32 : SPLIT_BF16;
+  const int bn = pick_bn(g.M, g.N);
+  const int Mp = round_up(2 * g.M, BM), Np = round_up(g.N, bn), Kp = round_up(6 * g.K, OpCfg<OPT>::BK);
+  if (split_workspace_bytes(g.M, g.N, g.K, g.batch, op) > work_bytes)
     return cuda_fail(cudaErrorInvalidValue, "split workspace too small", __FILE__, __LINE__);
   char* w = (char*)(((uintptr_t)work + 1023) & ~(uintptr_t)1023);
-  __nv_bfloat16* A3 = (__nv_bfloat16*)w;
-  w += ((size_t)Mp * Kp * 2 * g.batch + 1023) & ~(size_t)1023;
-  __nv_bfloat16* B3 = (__nv_bfloat16*)w;
-  w += ((size_t)Np * Kp * 2 * g.batch + 1023) & ~(size_t)1023;
+  T* A3 = (T*)w;
+  w += ((size_t)Mp * Kp * sizeof(T) * g.batch + 1023) & ~(size_t)1023;
+  T* B3 = (T*)w;
+  w += ((size_t)Np * Kp * sizeof(T) * g.batch + 1023) & ~(size_t)1023;
   float* C32 = (float*)w;
   if (g.batch > 65535 || g.M > 65535) return cuda_fail(cudaErrorInvalidValue, "split gemm grid", __FILE__, __LINE__);
   // zero K padding (columns 6K .. Kp) of both operands; the GEMM reads it
   if (Kp > 6 * g.K) {
-    const size_t pitch = (size_t)Kp * 2, width = (size_t)(Kp - 6 * g.K) * 2;
+    const size_t pitch = (size_t)Kp * sizeof(T), width = (size_t)(Kp - 6 * g.K) * sizeof(T);
     IPEPS_CUDA_TRY(cudaMemset2DAsync(A3 + 6 * g.K, pitch, 0, width, (size_t)Mp * g.batch, st));
     IPEPS_CUDA_TRY(cudaMemset2DAsync(B3 + 6 * g.K, pitch, 0, width, (size_t)Np * g.batch, st));
   }
   const dim3 pblk(PT, 8);
   const dim3 pa((g.K + PT - 1) / PT, (g.M + PT - 1) / PT, g.batch);
   const dim3 pb((g.K + PT - 1) / PT, (g.N + PT - 1) / PT, g.batch);
-  IPEPS_LAUNCH(K_TC_PREP, 0, st, prep_a_kernel<<<pa, pblk, 0, st>>>(g, A3, Mp, Kp));
-  IPEPS_LAUNCH(K_TC_PREP, 0, st, prep_b_kernel<<<pb, pblk, 0, st>>>(g, B3, Np, Kp));
+  IPEPS_LAUNCH(K_TC_PREP, 0, st, prep_a_kernel<T><<<pa, pblk, 0, st>>>(g, A3, Mp, Kp));
+  IPEPS_LAUNCH(K_TC_PREP, 0, st, prep_b_kernel<T><<<pb, pblk, 0, st>>>(g, B3, Np, Kp));
   IPEPS_CUDA_TRY(cudaGetLastError());
   const double algo = 8.0 * g.M * (double)g.N * g.K * g.batch;   // the complex product's own flops
-  if (int rc = gemm_bf16_raw(A3, B3, C32, Mp, Np, Kp, g.batch, bn, algo, err, st, g.skip, g.skip_mod))
-    return rc;
+  if (int rc = gemm_raw<OPT>(A3, B3, C32, Mp, Np, Kp, g.batch, bn, algo, err, st, g.skip, g.skip_mod)) return rc;
   const dim3 gc((g.N + 255) / 256, g.M, g.batch);
   IPEPS_LAUNCH(K_TC_PREP, 0, st, gather_c_kernel<<<gc, 256, 0, st>>>(g, C32, Mp, Np));
   IPEPS_CUDA_TRY(cudaGetLastError());
   return 0;
+}
+
+int zgemm_split(const GemmDesc& g, int op, void* work, size_t work_bytes, unsigned* err, cudaStream_t st) {
+  if (g.M <= 0 || g.N <= 0 || g.K <= 0 || g.batch <= 0) return 0;
+  if (op == SPLIT_TF32) return zgemm_split_t<float, OP_TF32>(g, work, work_bytes, err, st);
+  return zgemm_split_t<__nv_bfloat16, OP_BF16>(g, work, work_bytes, err, st);
 }
 
 }  // namespace tc
