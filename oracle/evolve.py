@@ -21,7 +21,9 @@ def ctm_state(GA, GB, lam):
     return A, B, a
 
 
-PROBE_NOISE = 1e-6
+PROBE_NOISE = 1e-6      # stability probe: relative kick of the converged environment
+SPLIT_NOISE = 1e-4      # robustness probe at the split-precision path's noise scale
+ROUNDING_KICK = 1e-13   # conditioning probe: relative kick of the site tensors
 PROBE_SEED = 12345
 
 
@@ -42,7 +44,12 @@ def converge_and_measure(GA, GB, lam, env, p, tol, max_sweeps, probe_sweeps=0):
     point the perturbation dies out and drift stays at the convergence level; at a fixed point
     the CTMRG map departs from (an unstable one) or where several attractors lie close together,
     the perturbed run ends elsewhere and drift is large: such a readout is not a unique result of
-    the method."""
+    the method.  ``drift_split`` repeats the probe with a relative 1e-4 kick (the noise scale of the
+    split-precision contractions).  ``sensitivity`` measures how well FP64 arithmetic determines the
+    readout: the site tensors are kicked by a relative 1e-13 (the size of rounding differences between
+    two correct implementations) and the environment re-converged; where the fixed point is
+    ill-conditioned (slow contraction, a small gap at the chi cut) the readout moves by far more than
+    1e-13."""
     A, B, a = ctm_state(GA, GB, lam)
     if env is None:
         env = ctmrg.init_env(a, 2, 2, p['chi'], p['D'])
@@ -56,19 +63,46 @@ def converge_and_measure(GA, GB, lam, env, p, tol, max_sweeps, probe_sweeps=0):
     obs.update(ctm_sweeps=sweeps, ctm_delta=delta, ctm_stop=stop,
                c8_margin=float(min(m for m, _ in last)), c8_level=float(max(v for _, v in last)))
     if probe_sweeps > 0:
-        rng = np.random.default_rng(PROBE_SEED)
-        e2 = env.copy()
-        for group in (e2.C, e2.T):
-            for tens in group:
-                for key in sorted(tens):
-                    t = tens[key]
-                    noise = rng.standard_normal(t.shape) + 1j * rng.standard_normal(t.shape)
-                    tens[key] = t + PROBE_NOISE * np.abs(t).max() * noise
-        e2, n2, d2 = ctmrg.ctmrg(a, e2, p['chi'], tol=tol, max_sweeps=probe_sweeps, cut_rel=cut_rel)
-        before, after = _site_obs(A, B, env, p), _site_obs(A, B, e2, p)
+        before = _site_obs(A, B, env, p)
+
+        def reconverge(e_start, a_used):
+            e2, n2, _ = ctmrg.ctmrg(a_used, e_start, p['chi'], tol=tol, max_sweeps=probe_sweeps, cut_rel=cut_rel)
+            return e2, n2
+
+        # stability: the environment kicked by a relative PROBE_NOISE
+        e2, n2 = reconverge(_kick_env(env, PROBE_NOISE, PROBE_SEED), a)
+        after = _site_obs(A, B, e2, p)
         obs['drift'] = float(max(abs(after[k] - before[k]) for k in before))
         obs['probe_sweeps'] = n2
+        # robustness at the split path's noise scale: a relative 1e-4 kick of the environment
+        e3, _ = reconverge(_kick_env(env, SPLIT_NOISE, PROBE_SEED + 1), a)
+        after = _site_obs(A, B, e3, p)
+        obs['drift_split'] = float(max(abs(after[k] - before[k]) for k in before))
+        # conditioning: the site tensors kicked by a relative ROUNDING_KICK (the size of rounding
+        # differences between two correct implementations), re-converged from the converged
+        # environment; the readout moves by ~ROUNDING_KICK directly plus whatever the fixed point's
+        # sensitivity adds
+        rng = np.random.default_rng(PROBE_SEED + 2)
+        Ak, Bk = [X * (1.0 + ROUNDING_KICK * (rng.standard_normal(X.shape) + 1j * rng.standard_normal(X.shape)))
+                  for X in (A, B)]
+        ak = ctmrg.checkerboard(ctmrg.double_layer(Ak), ctmrg.double_layer(Bk))
+        e4, _ = reconverge(env.copy(), ak)
+        after = _site_obs(Ak, Bk, e4, p)
+        obs['sensitivity'] = float(max(abs(after[k] - before[k]) for k in before))
     return env, obs
+
+
+def _kick_env(env, rel, seed):
+    """A copy of the environment with every tensor perturbed by a seeded relative kick."""
+    rng = np.random.default_rng(seed)
+    e2 = env.copy()
+    for group in (e2.C, e2.T):
+        for tens in group:
+            for key in sorted(tens):
+                t = tens[key]
+                noise = rng.standard_normal(t.shape) + 1j * rng.standard_normal(t.shape)
+                tens[key] = t + rel * np.abs(t).max() * noise
+    return e2
 
 
 def _site_obs(A, B, env, p):

@@ -30,7 +30,7 @@ PROBE = 100
 
 KEYS = ("t", "nA", "nB", "imbalance", "tauzA", "tauzB", "energy", "purityA", "trunc_err_acc",
         "ctm_sweeps", "ctm_delta", "ctm_stop", "c8_margin", "c8_level", "drift", "probe_sweeps",
-        "renyi1A", "renyi_halfA", "renyi2A")
+        "drift_split", "sensitivity", "renyi1A", "renyi_halfA", "renyi2A")
 
 
 def _val(v):
@@ -44,7 +44,7 @@ def _val(v):
 def _dump(path, params, out, seconds):
     rows = []
     for o in out:
-        r = {k: _val(o[k]) for k in KEYS}
+        r = {k: _val(o[k]) for k in KEYS if k in o}
         r["lam"] = [[float(x) for x in row] for row in o["lam"]]
         # the same readout converged from the traced start (gauge independent, see evolve.run)
         r["cold"] = {k: _val(o["cold"][k]) for k in KEYS if k in o["cold"]}

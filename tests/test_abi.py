@@ -34,10 +34,10 @@ def test_every_declared_function_is_exported(lib, header):
 def _params(**kw):
     import paper_1910_11359_gb300._lib as L
     p = dict(J=[1.0, 1.0], V=[1.0, 0.0], h=[5.0, 2.0], D=3, chi=18, order=2, dt=0.05, precision=0,
-             seed=0)
+             seed=0, d_A=2)
     p.update(kw)
     return L._params(p["J"], p["V"], p["h"], p["D"], p["chi"], p["order"], p["dt"], p["precision"],
-                     p["seed"])
+                     p["seed"], d_A=p["d_A"])
 
 
 def test_footprint_sizing_without_device():
@@ -49,6 +49,8 @@ def test_footprint_sizing_without_device():
     assert 0 < one < three < 3.5 * one          # per-instance arrays plus shared tables
     assert big > 2 * one
     assert split > big                           # the tensor-core operand workspace
+    levels3 = pkg.footprint_bytes([1.0], [1.0], [5.0], D=3, chi=18, d_A=3)
+    assert levels3 > one                         # d = 6: larger site tensors, gates and readout
 
 
 @pytest.mark.parametrize("kw,status", [
@@ -56,8 +58,10 @@ def test_footprint_sizing_without_device():
     (dict(order=3), 1),               # Trotter order
     (dict(D=0), 1),
     (dict(precision=7), 1),
-    (dict(precision=2), 8),           # TF32x3: declared, not implemented in this build
     (dict(chi=4096), 8),              # beyond the supported chi
+    (dict(d_A=6), 1),                 # more disorder levels than the library takes
+    (dict(d_A=1), 1),
+    (dict(d_A=3, D=2, chi=8), 8),     # the reduced simple update needs D^2 >= d = 6
 ])
 def test_invalid_parameters_are_rejected_before_any_device_call(lib, kw, status):
     import paper_1910_11359_gb300._lib as L

@@ -115,3 +115,67 @@ def test_jacobi_svd_tall_blocks(m, n):
         rec = (U[b] * S[b]) @ V[b].conj().T
         assert np.max(np.abs(rec - A[b])) < 1e-12 * s_ref[0]
         assert np.max(np.abs(V[b].conj().T @ V[b] - np.eye(n))) < 1e-13
+
+
+@pytest.mark.parametrize("N,k,batch", [(162, 26, 3), (512, 40, 2), (2592, 80, 1)])
+def test_orth_cholesky_qr(N, k, batch):
+    """Column-scaled Cholesky QR: orthonormal columns (Q^+ Q = I to rounding) spanning the input's
+    (Q Q^+ X = X), on blocks shaped like the projector subspace blocks.  The columns of X are scaled
+    over ten orders of magnitude, as the blocks M V are; one column is exactly zero and must stay
+    zero."""
+    rng = np.random.default_rng(11)
+    X = rng.standard_normal((batch, N, k)) + 1j * rng.standard_normal((batch, N, k))
+    X *= 10.0 ** (-10.0 * np.arange(k) / k)[None, None, :]
+    X[:, :, k // 2] = 0.0
+    dX = _dev(X)
+    dQ = torch.zeros_like(dX)
+    fail = (ctypes.c_int * batch)()
+    rc = _lib().ipeps_kernel_orth(N, k, batch, _p(dX), _p(dQ), 3, fail, None)
+    assert rc == 0
+    assert list(fail) == [0] * batch
+    Q = dQ.cpu().numpy()
+    live = [j for j in range(k) if j != k // 2]
+    for b in range(batch):
+        q = Q[b][:, live]
+        assert np.max(np.abs(q.conj().T @ q - np.eye(len(live)))) < 1e-13
+        assert np.max(np.abs(Q[b][:, k // 2])) == 0.0
+        proj = q @ (q.conj().T @ X[b])
+        err = np.max(np.abs(proj - X[b]) / np.maximum(np.linalg.norm(X[b], axis=0), 1e-300)[None, :])
+        assert err < 1e-11, err
+
+
+def test_orth_flags_dependent_columns():
+    """Columns that are exactly parallel cannot be orthonormalised by Cholesky QR: the problem is
+    flagged (and the caller falls back) rather than returning a Q that is not orthonormal."""
+    N, k = 100, 8
+    rng = np.random.default_rng(3)
+    X = rng.standard_normal((1, N, k)) + 1j * rng.standard_normal((1, N, k))
+    X[0, :, 5] = 3.0 * X[0, :, 2]
+    dX = _dev(X)
+    dQ = torch.zeros_like(dX)
+    fail = (ctypes.c_int * 1)()
+    rc = _lib().ipeps_kernel_orth(N, k, 1, _p(dX), _p(dQ), 2, fail, None)
+    assert rc == 0
+    if not fail[0]:
+        q = dQ.cpu().numpy()[0]
+        assert np.max(np.abs(q.conj().T @ q - np.eye(k))) < 1e-10
+
+
+def test_orth_ill_conditioned_block():
+    """A block whose columns stay far from orthogonal after scaling (singular values spread over ten
+    orders of magnitude, mixed by a random unitary: condition ~1e10) is orthonormalised by the
+    three-pass shifted Cholesky QR and spans the input to its conditioning."""
+    N, k = 300, 40
+    rng = np.random.default_rng(5)
+    base = np.linalg.qr(rng.standard_normal((N, k)) + 1j * rng.standard_normal((N, k)))[0]
+    W = np.linalg.qr(rng.standard_normal((k, k)) + 1j * rng.standard_normal((k, k)))[0]
+    X = ((base * 10.0 ** (-10.0 * np.arange(k) / (k - 1))) @ W.conj().T)[None]
+    dX = _dev(X)
+    dQ = torch.zeros_like(dX)
+    fail = (ctypes.c_int * 1)()
+    assert _lib().ipeps_kernel_orth(N, k, 1, _p(dX), _p(dQ), 3, fail, None) == 0
+    assert fail[0] == 0
+    q = dQ.cpu().numpy()[0]
+    assert np.max(np.abs(q.conj().T @ q - np.eye(k))) < 1e-12
+    err = np.linalg.norm(q @ (q.conj().T @ X[0]) - X[0]) / np.linalg.norm(X[0])
+    assert err < 1e-12

@@ -39,3 +39,20 @@ def test_batched_split_sweep_imbalance_vs_fp64():
                 for k in ("imbalance", "nA", "nB"))
     print("split vs FP64 sweep: max abs difference of imbalance, nA, nB %.1e" % worst)
     assert worst < 1e-4
+
+
+def test_batched_sweep_matches_solo_runs_split():
+    """Split precision: every kernel's arithmetic is per problem (tensor-core tiles, the FP64
+    projector pipeline, skip flags), so an instance's readouts do not depend on the batch it runs
+    in: the batched sweep equals the points run one at a time."""
+    from paper_1910_11359_gb300.sweep import disorder_sweep
+    batched = disorder_sweep(POINTS, t_max=0.2, meas_every=0.1, precision=1, concurrent=True, tol=1e-6,
+                             max_sweeps=100)
+    worst = 0.0
+    for i, p in enumerate(POINTS):
+        solo = disorder_sweep([p], t_max=0.2, meas_every=0.1, precision=1, concurrent=False, tol=1e-6,
+                              max_sweeps=100)[0]
+        for a, b in zip(solo, batched[i]):
+            worst = max(worst, max(abs(a[k] - b[k]) for k in KEYS))
+    print("batched vs solo, split: max abs difference %.1e" % worst)
+    assert worst < 1e-9
