@@ -52,8 +52,9 @@ typedef struct {
   double dt;                /* Trotter step */
   int precision;            /* IPEPS_FP64; IPEPS_SPLIT_BF16X3 or IPEPS_SPLIT_TF32X3: the large
                                contractions on the tcgen05 tensor cores as 3-term split products
-                               (two BF16 / TF32 terms per value, FP32 accumulation; relative error
-                               ~1e-5 / ~1e-7), projectors, simple update and readout in FP64 */
+                               (two BF16 / TF32 terms per value, FP32 accumulation, per K tile for
+                               TF32; relative error ~2e-5 / ~1e-6), projectors, simple update and
+                               readout in FP64 */
   unsigned long long seed;  /* seeds random starting vectors of iterative solvers */
   const double* J;          /* [batch] hopping, host, copied */
   const double* V;          /* [batch] nearest-neighbour interaction, host, copied */
@@ -108,8 +109,16 @@ ipeps_status ipeps_trotter_step(ipeps_h h, int n_steps, double* trunc_err_out);
  * 1e-6.  The first call starts from the traced
  * double layers, later calls from the previous environment.  sweeps_out: host int[batch] or NULL;
  * delta_out: host double[batch] or NULL (last change).  Returns IPEPS_ENOCONV when an instance
- * reached max_sweeps without converging (its environment is still usable). */
+ * reached max_sweeps without converging (its environment is still usable).  Once every projector
+ * has been warm-started (after the first sweep from a fresh environment), the remaining sweeps run
+ * as one CUDA graph in which the device decides when to stop (conditional WHILE nodes over the
+ * sweeps and over each projector's subspace rounds); the results are those of the eager loop. */
 ipeps_status ctmrg_converge(ipeps_h h, double tol, int max_sweeps, int* sweeps_out, double* delta_out);
+
+/* enable != 0 (the default): ctmrg_converge uses the convergence graph described above; 0: every
+ * sweep is issued from the host, with a readback of the converged flags after each.  Launch timing
+ * (ipeps_profile_enable) always uses the host loop. */
+ipeps_status ipeps_set_graphs(ipeps_h h, int enable);
 
 /* Discard the environment; the next ctmrg_converge starts from the traced double layers. */
 ipeps_status ctmrg_reset(ipeps_h h);

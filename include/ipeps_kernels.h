@@ -62,6 +62,17 @@ int ipeps_kernel_zgemm_split(int M, int N, int K, int batch, int opA, int opB,
                              const double* B, long long ldb, long long sB,
                              double* C, long long ldc, long long sC, void* stream);
 
+/* The same product with TF32 terms (kind::tf32; two TF32 values per FP64 value, three products):
+ * each K tile of 32 TF32 values is accumulated from zero in its own TMEM buffer and the tiles are
+ * summed in FP32 registers with round-to-nearest, so the tensor cores' truncating accumulation adds
+ * the bias of four MMAs per tile instead of one growing with K.  Relative error (largest over the
+ * outputs) ~1e-6 of |a| |b| sqrt(K), growing like the square root of the number of K tiles; BF16x3:
+ * ~2e-5.  Arguments, layout, ownership and errors as ipeps_kernel_zgemm_split. */
+int ipeps_kernel_zgemm_split_tf32(int M, int N, int K, int batch, int opA, int opB,
+                                  const double* A, long long lda, long long sA,
+                                  const double* B, long long ldb, long long sB,
+                                  double* C, long long ldc, long long sC, void* stream);
+
 /* out = in permuted: out axis j is in axis perm[j] (rank <= 8, dims[] of the input). */
 int ipeps_kernel_permute(const double* in, double* out, int rank, const int* dims,
                          const int* perm, int batch, long long s_in, long long s_out, void* stream);

@@ -50,7 +50,7 @@ EXPORTS = ["ipeps_init", "ipeps_set_tensors", "ipeps_trotter_step", "ctmrg_conve
            "ipeps_profile_enable", "ipeps_profile_classes", "ipeps_profile_name", "ipeps_profile_read",
            "ipeps_kernel_fp64_peak", "ipeps_kernel_svd_noalloc", "ipeps_kernel_zgemm_split",
            "ipeps_get_env", "ipeps_set_env", "ipeps_profile_tc_executed", "ipeps_profile_counters",
-           "ipeps_kernel_orth", "ipeps_kernel_zgemm_split_tf32"]
+           "ipeps_kernel_orth", "ipeps_kernel_zgemm_split_tf32", "ipeps_set_graphs"]
 
 
 def lib():
@@ -69,6 +69,7 @@ def lib():
     L.ipeps_trotter_step.argtypes = [vp, i, dp]
     L.ctmrg_converge.argtypes = [vp, d, i, ip, dp]
     L.ctmrg_reset.argtypes = [vp]
+    L.ipeps_set_graphs.argtypes = [vp, i]
     L.ipeps_measure.argtypes = [vp, P(Obs)]
     L.ipeps_corner_spectrum.argtypes = [vp, i, i, i, dp]
     L.ipeps_get_lambda.argtypes = [vp, dp]
@@ -180,6 +181,10 @@ class IPEPS:
 
     def ctmrg_reset(self):
         _check(lib().ctmrg_reset(self._h), self._h)
+
+    def set_graphs(self, enable=True):
+        """Converge through one CUDA graph (default) or from the host loop."""
+        _check(lib().ipeps_set_graphs(self._h, 1 if enable else 0), self._h)
 
     def measure(self):
         arr = (Obs * self.batch)()

@@ -10,6 +10,7 @@
 #include "measure.cuh"
 #include "model.cuh"
 #include "orth.cuh"
+#include "prof.cuh"
 #include "tc_gemm.cuh"
 
 using namespace ipeps;
@@ -109,6 +110,7 @@ void carve_all(ipeps_ctx* x) {
   c.bondop = a.take<cplx>((size_t)B * d * d * d * d);
   c.derr = a.take<unsigned>(1);
   c.dflag = a.take<int>(1);
+  c.loopctl = a.take<int>(4);
   SuWork& s = c.su;
   s.Amat = a.take<cplx>((size_t)B * D3 * n); s.Bmat = a.take<cplx>((size_t)B * D3 * n);
   s.UA = a.take<cplx>((size_t)B * D3 * n); s.UB = a.take<cplx>((size_t)B * D3 * n);
@@ -223,7 +225,7 @@ ipeps_status ipeps_init(const ipeps_params* p, void* cuda_stream, ipeps_h* out) 
     return fail(nullptr, IPEPS_ENOMEM, "cudaMalloc of the pointer tables failed");
   }
   c.pool.base = (void**)c.dev_ptrs;
-  if (cudaHostAlloc((void**)&c.hflag, sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
+  if (cudaHostAlloc((void**)&c.hflag, 4 * sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(c.dev_ptrs);
     cudaFree(c.dev_base);
@@ -276,10 +278,18 @@ bad:
 ipeps_status ipeps_destroy(ipeps_h h) {
   if (!h) return IPEPS_OK;
   cudaStreamSynchronize(h->c.st);
+  if (h->c.conv_exec) cudaGraphExecDestroy(h->c.conv_exec);
+  if (h->c.cap_st) cudaStreamDestroy(h->c.cap_st);
   cudaFreeHost(h->c.hflag);
   cudaFree(h->c.dev_ptrs);
   cudaFree(h->c.dev_base);
   delete h;
+  return IPEPS_OK;
+}
+
+ipeps_status ipeps_set_graphs(ipeps_h h, int enable) {
+  if (!h) return fail(h, IPEPS_EINVAL, "NULL handle");
+  h->c.graphs = enable != 0;
   return IPEPS_OK;
 }
 
@@ -325,6 +335,63 @@ ipeps_status ctmrg_reset(ipeps_h h) {
   return IPEPS_OK;
 }
 
+// End of a sweep inside the convergence graph: counts it and continues while fewer than the limit
+// ran and (with a tolerance) some instance is still open.
+__global__ void conv_test_kernel(const int* frozen, int B, int* ctl, int use_tol, cudaGraphConditionalHandle h) {
+  __shared__ int open;
+  if (threadIdx.x == 0) open = 0;
+  __syncthreads();
+  for (int b = threadIdx.x; b < B; b += blockDim.x)
+    if (!frozen[b]) open = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int s = ctl[0] + 1;
+    ctl[0] = s;
+    loop_set(h, 1, s < ctl[1] && (!use_tol || open));
+  }
+}
+
+// Captures the convergence loop (sweep, corner spectra, test) as one graph: a WHILE node over
+// sweeps whose body holds one WHILE node per projector's subspace rounds.
+static int capture_converge(Ctx& c, double tol_eff, bool use_tol) {
+  if (!c.cap_st) IPEPS_CUDA_TRY(cudaStreamCreateWithFlags(&c.cap_st, cudaStreamNonBlocking));
+  GraphBuilder gb;
+  cudaGraphExec_t exec = nullptr;
+  // the routines below issue their work on c.st: point it at the capture stream meanwhile (nothing
+  // runs during a capture; the graph is launched on the handle's own stream)
+  const cudaStream_t user_st = c.st;
+  c.st = c.cap_st;
+  int rc = gb.begin(c.st);
+  cudaGraphConditionalHandle hs = 0;
+  c.gb = &gb;
+  if (!rc) rc = gb.loop_begin(c.loopctl, &hs);
+  if (!rc) rc = ctm_sweep(c);
+  if (!rc) rc = ctm_spectra(c, tol_eff, 0);
+  if (!rc) {
+    conv_test_kernel<<<1, 128, 0, c.st>>>(c.w.frozen, c.B, c.loopctl, use_tol ? 1 : 0, hs);
+    rc = cuda_fail(cudaGetLastError(), "conv test launch", __FILE__, __LINE__);
+  }
+  if (!rc) rc = gb.loop_end();
+  if (!rc) rc = gb.end(&exec);
+  c.gb = nullptr;
+  c.st = user_st;
+  if (rc) {
+    gb.abandon();
+    return rc;
+  }
+  if (c.conv_exec) cudaGraphExecDestroy(c.conv_exec);
+  c.conv_exec = exec;
+  c.conv_tol = use_tol ? tol_eff : -1.0;
+  return 0;
+}
+
+static bool slots_warm(const Ctx& c) {
+  for (int f = 0; f < 4; ++f)
+    for (int x = 0; x < 2; ++x)
+      if (!c.slot_warm[f][x]) return false;
+  return true;
+}
+
 ipeps_status ctmrg_converge(ipeps_h h, double tol, int max_sweeps, int* sweeps_out, double* delta_out) {
   if (!h || max_sweeps < 1) return fail(h, IPEPS_EINVAL, "bad handle or max_sweeps");
   Ctx& c = h->c;
@@ -341,18 +408,34 @@ ipeps_status ctmrg_converge(ipeps_h h, double tol, int max_sweeps, int* sweeps_o
   // stall rule covers the rest)
   const double floor_tol = split_tol_floor(c.precision);
   const double tol_eff = tol > 0.0 ? (tol < floor_tol ? floor_tol : tol) : -1.0;
-  for (int s = 0; s < max_sweeps; ++s) {
+  // Sweeps run eagerly (a host readback of the frozen flags after each) until every projector slot
+  // has its warm start; the rest run as one launch of the convergence graph, in which the device
+  // decides when to stop.  Both run the same kernels in the same order.
+  int s = 0;
+  bool all = false;
+  const bool graphs = c.graphs && !prof_enabled();
+  while (s < max_sweeps && !all && !(graphs && slots_warm(c))) {
     if ((rc = ctm_sweep(c))) return from_rc(h, rc);
     if ((rc = ctm_spectra(c, tol_eff, 0))) return from_rc(h, rc);
+    ++s;
     if (tol > 0.0) {
       if (cudaMemcpyAsync(frozen.data(), c.w.frozen, sizeof(int) * B, cudaMemcpyDeviceToHost, c.st) != cudaSuccess)
         return from_rc(h, cuda_fail(cudaGetLastError(), "frozen copy", __FILE__, __LINE__));
       ipeps_status st = check_dev(h);
       if (st != IPEPS_OK && st != IPEPS_ENOCONV) return st;
-      bool all = true;
+      all = true;
       for (int b = 0; b < B; ++b) all = all && frozen[b];
-      if (all) break;
     }
+  }
+  if (s < max_sweeps && !all) {
+    const double key = tol > 0.0 ? tol_eff : -1.0;
+    if (!c.conv_exec || c.conv_tol != key) {
+      if ((rc = capture_converge(c, tol_eff, tol > 0.0))) return from_rc(h, rc);
+    }
+    c.hflag[1] = max_sweeps - s;
+    if (cudaMemcpyAsync(c.loopctl + 1, c.hflag + 1, sizeof(int), cudaMemcpyHostToDevice, c.st) != cudaSuccess ||
+        cudaGraphLaunch(c.conv_exec, c.st) != cudaSuccess)
+      return from_rc(h, cuda_fail(cudaGetLastError(), "convergence graph launch", __FILE__, __LINE__));
   }
   h->last_sweeps.assign(B, 0);
   h->last_delta.assign(B, 0.0);
@@ -507,7 +590,8 @@ int ipeps_kernel_orth(int N, int k, int batch, const double* X, double* Q, int p
   OrthDesc d;
   d.N = N; d.k = k; d.batch = batch;
   d.X = (const cplx*)X; d.sX = (long long)N * k; d.Q = (cplx*)Q; d.sQ = (long long)N * k;
-  d.work = work; d.work_bytes = wb; d.skip = nullptr; d.fail = dfail; d.passes = passes; d.dev_fail = 1e-2;
+  d.work = work; d.work_bytes = wb; d.skip = nullptr; d.fail = dfail; d.passes = passes; d.shifted = true;
+  d.dev_fail = 1e-2;
   if (!rc) rc = orth_cqr(d, st);
   std::vector<int> hf(batch, 0);
   if (!rc && (cudaMemcpyAsync(hf.data(), dfail, sizeof(int) * batch, cudaMemcpyDeviceToHost, st) != cudaSuccess ||

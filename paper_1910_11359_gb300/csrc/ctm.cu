@@ -595,9 +595,12 @@ __global__ void sub_init_kernel(int* done, int* rounds, const int* frozen, int B
 // Columns of Z = M^+ U_y with negligible norm (M has rank below k, or u_j is a zero column) are
 // replaced by random columns before Z is orthonormalised, so the block keeps full rank.
 __global__ void sub_refill_kernel(cplx* Z, int N, int k, unsigned long long seed,
-                                  unsigned long long stream, const int* skip, int B) {
+                                  unsigned long long stream_base, const int* round_ctr, const int* skip,
+                                  int B) {
   const int q = blockIdx.x;
   if (skip[q]) return;
+  // draws of round r (the test kernel has already counted it: *round_ctr = r + 1)
+  const unsigned long long stream = stream_base + (unsigned long long)(*round_ctr - 1);
   const unsigned long long cut = (unsigned long long)(q / B);   // batch-independent draws
   cplx* Zq = Z + (size_t)q * N * k;
   __shared__ double nrm[256];
@@ -682,18 +685,26 @@ __global__ void orth_route_kernel(const int* done, const int* fail, int* skip_ne
 }
 
 // flag = 1 when every subspace problem has converged (or is skipped)
-__global__ void sub_all_done_kernel(const int* done, int n, int* flag) {
+// End of a subspace round: counts it in *ctr, writes whether every problem has converged to *flag
+// and (graph mode) continues the loop while some problem is open and fewer than `rounds` ran.
+__global__ void sub_test_kernel(const int* done, int n, int* ctr, int rounds, cudaGraphConditionalHandle h,
+                                int graph, int* flag) {
   __shared__ int any_open;
   if (threadIdx.x == 0) any_open = 0;
   __syncthreads();
   for (int q = threadIdx.x; q < n; q += blockDim.x)
     if (!done[q]) any_open = 1;
   __syncthreads();
-  if (threadIdx.x == 0) *flag = any_open ? 0 : 1;
+  if (threadIdx.x == 0) {
+    const int r = *ctr + 1;
+    *ctr = r;
+    *flag = any_open ? 0 : 1;
+    loop_set(h, graph, any_open && r < rounds);
+  }
 }
 
-// rounds after which the host reads back whether every problem has converged (a readback is a
-// stream synchronisation, so they are spaced out geometrically)
+// eager mode: rounds after which the host reads back whether every problem has converged (a
+// readback is a stream synchronisation, so they are spaced out geometrically)
 static bool sub_checkpoint(int rounds_done) {
   const int marks[] = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48};
   for (int m : marks)
@@ -715,7 +726,11 @@ static bool sub_checkpoint(int rounds_done) {
 //  * otherwise the one-sided Jacobi SVD of the N x k blocks themselves.
 // Converged problems are skipped by every later launch.  The iteration starts from the slot's
 // previous right vectors (random on the slot's first use); at most 40 rounds per call (60 on first
-// use; converged problems make the later rounds' launches exit at once).
+// use; converged problems make the later rounds' launches exit at once).  The round loop is a
+// conditional WHILE node when a convergence graph is being captured (c.gb): the test kernel ends
+// it on the device; eagerly, the host reads the same kernel's flag at the checkpoints.  The second
+// half of a round (refill, orthonormalisation of Z into the next V) then also runs after the last
+// round; it writes only the next start block, which nothing reads.
 static int subspace_svd(Ctx& c, int f, int x, const cplx* R, const cplx* Rt) {
   CtmWork& w = c.w;
   const int B = c.B, N = c.N, k = c.k, chi = c.chi;
@@ -744,7 +759,10 @@ static int subspace_svd(Ctx& c, int f, int x, const cplx* R, const cplx* Rt) {
   bd.tol = 4e-16 * k; bd.skip = w.skip_new; bd.gwork = nullptr; bd.gwork_bytes = 0;
   OrthDesc od;
   od.N = N; od.k = k; od.batch = 2 * B; od.work = w.orth_work; od.work_bytes = w.orth_bytes;
-  od.skip = w.sub_done; od.fail = w.ofail; od.passes = 3; od.dev_fail = 1e-2;
+  // warm rounds: blocks close to orthonormal after column scaling; a shifted pass and a plain pass
+  // whose input must already be within 1e-2 of orthonormal (else the tall Jacobi takes over);
+  // cold rounds (random start): the full three-pass shifted Cholesky QR
+  od.skip = w.sub_done; od.fail = w.ofail; od.passes = warm ? 2 : 3; od.shifted = true; od.dev_fail = 1e-2;
   const int ncheck = chi + 1 < k ? chi + 1 : k;
   const double rtol = 1e-14, stag = 1e-12;
   auto route = [&]() -> int {
@@ -754,7 +772,15 @@ static int subspace_svd(Ctx& c, int f, int x, const cplx* R, const cplx* Rt) {
     IPEPS_CUDA_TRY(cudaGetLastError());
     return 0;
   };
-  for (int it = 0; it < rounds; ++it) {
+  const int graph = c.gb ? 1 : 0;
+  int* rctr = c.loopctl + 2;
+  cudaGraphConditionalHandle hl = 0;
+  if (graph) {
+    if ((rc = c.gb->loop_begin(rctr, &hl))) return rc;
+  } else {
+    IPEPS_LAUNCH(K_PROJ_PREP, 0, st, loop_arm_kernel<<<1, 32, 0, st>>>(0, 0, rctr));
+  }
+  for (int it = 0; it < (graph ? 1 : rounds); ++it) {
     GemmDesc g = gd(N, k, N, 2 * B);            // Y = M V
     g.A = w.M; g.sA = N2; g.lda = N; g.B = w.Vw; g.sB = Nk; g.ldb = k;
     g.C = w.Ysub; g.sC = Nk; g.ldc = k; g.skip = w.sub_done;
@@ -783,15 +809,18 @@ static int subspace_svd(Ctx& c, int f, int x, const cplx* R, const cplx* Rt) {
                  sub_residual_kernel<<<2 * B, 256, 0, st>>>(w.Zsub, slot, w.Sy, N, k, ncheck, rtol,
                                                             stag, w.sub_done, w.sub_rounds, w.sub_res,
                                                             prof_device_counters()));
-    if (it + 1 == rounds) break;
-    if (sub_checkpoint(it + 1)) {
-      IPEPS_LAUNCH(K_PROJ_PREP, 0, st, sub_all_done_kernel<<<1, 128, 0, st>>>(w.sub_done, 2 * B, c.dflag));
-      IPEPS_CUDA_TRY(cudaMemcpyAsync(c.hflag, c.dflag, sizeof(int), cudaMemcpyDeviceToHost, st));
-      IPEPS_CUDA_TRY(cudaStreamSynchronize(st));
-      if (*c.hflag) break;
+    IPEPS_LAUNCH(K_PROJ_PREP, 0, st,
+                 sub_test_kernel<<<1, 128, 0, st>>>(w.sub_done, 2 * B, rctr, rounds, hl, graph, c.dflag));
+    if (!graph) {
+      if (it + 1 == rounds) break;
+      if (sub_checkpoint(it + 1)) {
+        IPEPS_CUDA_TRY(cudaMemcpyAsync(c.hflag, c.dflag, sizeof(int), cudaMemcpyDeviceToHost, st));
+        IPEPS_CUDA_TRY(cudaStreamSynchronize(st));
+        if (*c.hflag) break;
+      }
     }
     IPEPS_LAUNCH(K_PROJ_PREP, 0, st,
-                 sub_refill_kernel<<<2 * B, 256, 0, st>>>(w.Zsub, N, k, c.seed, stream_id * 1000 + it,
+                 sub_refill_kernel<<<2 * B, 256, 0, st>>>(w.Zsub, N, k, c.seed, stream_id * 1000, rctr,
                                                           w.sub_done, B));
     if (c.orth) {
       IPEPS_CUDA_TRY(cudaMemsetAsync(w.ofail, 0, sizeof(int) * 2 * B, st));
@@ -803,6 +832,7 @@ static int subspace_svd(Ctx& c, int f, int x, const cplx* R, const cplx* Rt) {
                  sub_fill_kernel<<<2 * B, 256, 0, st>>>(w.Vz, nullptr, N, k, 0, c.seed, 0, w.Vw,
                                                         c.orth ? w.skip_old : w.sub_done, B));
   }
+  if (graph && (rc = c.gb->loop_end())) return rc;
   c.slot_warm[f][x] = true;
   IPEPS_LAUNCH(K_PROJ_PREP, 0, st,
                proj_prep_kernel<<<2 * B, 256, 2 * chi * sizeof(double), st>>>(w.Sy, k, k, w.Uy, slot, N, chi, k, Nk, w.Us,

@@ -4,6 +4,7 @@
 #include <vector>
 
 #include "arena.cuh"
+#include "graph.cuh"
 #include "linalg.cuh"
 #include "su.cuh"
 
@@ -121,7 +122,15 @@ struct Ctx {
   double t = 0.0;
   unsigned* derr = nullptr;
   int* dflag = nullptr;                   // device scratch flag (all subspace problems converged)
-  int* hflag = nullptr;                   // pinned host copy of dflag
+  int* hflag = nullptr;                   // pinned host ints: [0] copy of dflag, [1] sweep limit
+  // device-driven loops (graph.cuh): [0] sweep counter, [1] sweep limit, [2] subspace rounds
+  int* loopctl = nullptr;
+  GraphBuilder* gb = nullptr;             // non-null while a convergence graph is being captured
+  bool graphs = true;                     // converge through one CUDA graph once the slots are warm
+  cudaStream_t cap_st = nullptr;          // private stream the graph is captured on (st may be the
+                                          // legacy default stream, which cannot capture)
+  cudaGraphExec_t conv_exec = nullptr;    // cached convergence graph and the tolerance it was built for
+  double conv_tol = 0.0;
   std::string msg;
 
   long long N2() const { return (long long)N * N; }

@@ -11,6 +11,7 @@
 //   rho_v(p -> p+y)  = Lh_f1(rot p) . Lh_f3(rot^3 (p+y))                   half rotated by 180 deg)
 // The eight left halves needed (frames 0..3 x logical positions (0,0) [site A], (1,0) [site B])
 // are computed as one batch.
+#include <algorithm>
 #include <vector>
 
 #include "ctx.cuh"
@@ -183,14 +184,24 @@ size_t measure_bytes(int B, int d, int D, int chi) {
   return a.used;
 }
 
+// jobs per pass: as many of the 8 B left-half jobs as fit their intermediates in kMeasurePassBytes
+// (at least one)
+int measure_group(int B, int D, int chi) {
+  const long long D2 = (long long)D * D, T = (long long)chi * D2 * chi;
+  const size_t per_job = sizeof(cplx) * (size_t)(2 * T + T * D2 + 2 * T * D2 * D2);
+  const long long fit = (long long)(kMeasurePassBytes / per_job);
+  return (int)std::max(1LL, std::min(fit, 8LL * B));
+}
+
 void measure_carve(Arena& a, MeasureWork& w, int B, int d, int D, int chi) {
   const long long D2 = (long long)D * D;
   const long long T = chi * D2 * chi;
-  w.tl = a.take<cplx>((size_t)8 * B * T);
-  w.W1 = a.take<cplx>((size_t)8 * B * T * D2);
-  w.bl = a.take<cplx>((size_t)8 * B * T);
-  w.W2 = a.take<cplx>((size_t)8 * B * T * D2 * D2);
-  w.W2p = a.take<cplx>((size_t)8 * B * T * D2 * D2);
+  const long long G = w.group = measure_group(B, D, chi);
+  w.tl = a.take<cplx>((size_t)G * T);
+  w.W1 = a.take<cplx>((size_t)G * T * D2);
+  w.bl = a.take<cplx>((size_t)G * T);
+  w.W2 = a.take<cplx>((size_t)G * T * D2 * D2);
+  w.W2p = a.take<cplx>((size_t)G * T * D2 * D2);
   w.ao = a.take<cplx>((size_t)8 * B * d * d * D2 * D2 * D2 * D2);
   w.Lh = a.take<cplx>((size_t)8 * B * chi * chi * d * d * D2);
   w.RCt = a.take<cplx>((size_t)2 * B * T);
@@ -266,29 +277,36 @@ int measure_run(Ctx& c, MeasureWork& w, const MeasurePlan& m, double* host_out) 
                                                               w.ao + (size_t)(f * 2 + l) * B * aoper, f));
       IPEPS_CUDA_TRY(cudaGetLastError());
     }
-  GemmDesc g = gdm(chi, D2 * chi, chi, 8 * B);         // tl = C1 T1
-  g.Aptr = m.tlA; g.lda = chi; g.Bptr = m.tlB; g.ldb = D2 * chi; g.C = w.tl; g.sC = T; g.ldc = D2 * chi;
-  if ((rc = zgemm_f64(g, st))) return rc;
-  g = gdm(chi * D2, D2 * chi, chi, 8 * B);             // W1 = T4 tl -> [c4d][kL][kU][c1r]
-  g.Aptr = m.w1A; g.lda = chi; g.B = w.tl; g.sB = T; g.ldb = D2 * chi; g.C = w.W1; g.sC = T * D2;
-  g.ldc = D2 * chi;
-  if ((rc = zgemm_f64(g, st))) return rc;
-  g = gdm(chi * D2, chi, chi, 8 * B);                  // bl = T3 C4 -> [e3r][kD][c4d]
-  g.Aptr = m.blA; g.lda = chi; g.Bptr = m.blB; g.ldb = chi; g.C = w.bl; g.sC = T; g.ldc = chi;
-  if ((rc = zgemm_f64(g, st))) return rc;
-  g = gdm(chi * D2, D2 * D2 * chi, chi, 8 * B);        // W2 = bl W1 -> [e3r][kD][kL][kU][c1r]
-  g.A = w.bl; g.sA = T; g.lda = chi; g.B = w.W1; g.sB = T * D2; g.ldb = (long long)D2 * D2 * chi;
-  g.C = w.W2; g.sC = T * D2 * D2; g.ldc = (long long)D2 * D2 * chi;
-  if ((rc = zgemm_f64(g, st))) return rc;
-  {
-    const int dims[5] = {chi, D2, D2, D2, chi}, perm[5] = {0, 4, 3, 2, 1};
-    if ((rc = permute_c128(w.W2, w.W2p, 5, dims, perm, 8 * B, T * D2 * D2, T * D2 * D2, st))) return rc;
+  // left halves, in passes of w.group jobs (job = (f * 2 + l) * B + b)
+  const long long Lper = (long long)chi * chi * d * d * D2;
+  for (int j0 = 0; j0 < 8 * B; j0 += w.group) {
+    const int G = std::min(w.group, 8 * B - j0);
+    GemmDesc g = gdm(chi, D2 * chi, chi, G);             // tl = C1 T1
+    g.Aptr = m.tlA + j0; g.lda = chi; g.Bptr = m.tlB + j0; g.ldb = D2 * chi; g.C = w.tl; g.sC = T;
+    g.ldc = D2 * chi;
+    if ((rc = zgemm_f64(g, st))) return rc;
+    g = gdm(chi * D2, D2 * chi, chi, G);                 // W1 = T4 tl -> [c4d][kL][kU][c1r]
+    g.Aptr = m.w1A + j0; g.lda = chi; g.B = w.tl; g.sB = T; g.ldb = D2 * chi; g.C = w.W1; g.sC = T * D2;
+    g.ldc = D2 * chi;
+    if ((rc = zgemm_f64(g, st))) return rc;
+    g = gdm(chi * D2, chi, chi, G);                      // bl = T3 C4 -> [e3r][kD][c4d]
+    g.Aptr = m.blA + j0; g.lda = chi; g.Bptr = m.blB + j0; g.ldb = chi; g.C = w.bl; g.sC = T; g.ldc = chi;
+    if ((rc = zgemm_f64(g, st))) return rc;
+    g = gdm(chi * D2, D2 * D2 * chi, chi, G);            // W2 = bl W1 -> [e3r][kD][kL][kU][c1r]
+    g.A = w.bl; g.sA = T; g.lda = chi; g.B = w.W1; g.sB = T * D2; g.ldb = (long long)D2 * D2 * chi;
+    g.C = w.W2; g.sC = T * D2 * D2; g.ldc = (long long)D2 * D2 * chi;
+    if ((rc = zgemm_f64(g, st))) return rc;
+    {
+      const int dims[5] = {chi, D2, D2, D2, chi}, perm[5] = {0, 4, 3, 2, 1};
+      if ((rc = permute_c128(w.W2, w.W2p, 5, dims, perm, G, T * D2 * D2, T * D2 * D2, st))) return rc;
+    }
+    g = gdm(chi * chi, d * d * D2, D2 * D2 * D2, G);     // Lh = W2p aoP -> [e3r][c1r][s][s'][kR]
+    g.A = w.W2p; g.sA = T * D2 * D2; g.lda = (long long)D2 * D2 * D2;
+    g.Bptr = m.aoB + j0; g.ldb = (long long)d * d * D2;
+    g.C = w.Lh + (size_t)j0 * Lper; g.sC = Lper; g.ldc = (long long)d * d * D2;
+    if ((rc = zgemm_f64(g, st))) return rc;
   }
-  g = gdm(chi * chi, d * d * D2, D2 * D2 * D2, 8 * B); // Lh = W2p aoP -> [e3r][c1r][s][s'][kR]
-  g.A = w.W2p; g.sA = T * D2 * D2; g.lda = (long long)D2 * D2 * D2;
-  g.Bptr = m.aoB; g.ldb = (long long)d * d * D2;
-  g.C = w.Lh; g.sC = (long long)chi * chi * d * d * D2; g.ldc = (long long)d * d * D2;
-  if ((rc = zgemm_f64(g, st))) return rc;
+  GemmDesc g;
   // right column C2 T2 C3 at (0,0) and (1,0)
   g = gdm(chi, D2 * chi, chi, 2 * B);
   g.Aptr = m.rcA; g.lda = chi; g.Bptr = m.rcB; g.ldb = D2 * chi; g.C = w.RCt; g.sC = T; g.ldc = D2 * chi;

@@ -5,7 +5,7 @@
 // exact zeros and kept out of the factorisation), then orthonormalised by Cholesky QR passes: the
 // Gram matrix G = Xh^+ Xh (split over row blocks, the partial sums added in a fixed order so the
 // result does not depend on the launch), its Cholesky factor G = R^+ R and R^-1 in one CTA per
-// problem, and Q = Xh R^-1 as a batched GEMM.  The first pass adds the shift
+// problem, and Q = Xh R^-1 as a batched GEMM.  With OrthDesc::shifted the first pass adds the shift
 // 11 (N k + k (k + 1)) u ||Xh||_F^2 to the diagonal, which keeps the factorisation defined for
 // Gram matrices that are singular to working precision; the later passes are plain and bring the
 // columns to orthonormality at the rounding level (shifted Cholesky QR, Fukaya, Kannan,
@@ -100,36 +100,53 @@ __global__ void atb_reduce_kernel(const cplx* P, int k, int nsplit, cplx* C, lon
   }
 }
 
-// Cholesky G = R^+ R (R upper triangular) and R^-1 of one k x k problem per CTA, in shared memory.
+// 1 / sqrt(d) for d > 0 to FP64 accuracy: an FP32 seed (~23 bits; d is scaled by a power of 4 into
+// FP32 range first) refined by two Newton-Raphson steps y <- y (3 - d y^2) / 2, each of which
+// doubles the number of correct bits.  A handful of FP64 operations instead of a square root and a
+// division, which matters on the factorisation's sequential chain.
+__device__ __forceinline__ double rsqrt_nr(double d) {
+  int e;
+  const double m = frexp(d, &e);                           // d = m 2^e, m in [0.5, 1)
+  const int h = e / 2;                                      // d = (m 2^(e - 2h)) 4^h
+  const double ms = ldexp(m, e - 2 * h);
+  double y = (double)rsqrtf((float)ms);
+  y = y * (1.5 - 0.5 * ms * y * y);
+  y = y * (1.5 - 0.5 * ms * y * y);
+  return ldexp(y, -h);
+}
+
+// Cholesky G = R^+ R (R upper triangular) and R^-1 of one k x k problem per CTA, in shared memory;
+// G is the sum of the nsplit partial products P[q][p] of atb_partial_kernel.
 // Columns with c_j = 0 are decoupled (unit diagonal, zero off-diagonal), so zero columns of Xh stay
 // zero in Q.  shift_rel > 0 adds shift_rel * (number of live columns) to the diagonal.  fail[q] is
 // set when a pivot is not positive and finite, or when dev_fail > 0 and max |G - I| over the live
 // block (how far the input was from orthonormal, written to dev[q]) exceeds dev_fail.  Rinv is
 // written row-major (k x k).  R occupies the upper triangle of the shared array; R^-1, also upper
 // triangular, is built in its strict lower triangle (transposed) and a separate diagonal.
-__global__ void cholinv_kernel(const cplx* G, const double* c, int k, double shift_rel, cplx* Rinv,
-                               int* fail, double* dev, double dev_fail, const int* skip) {
+__global__ void cholinv_kernel(const cplx* P, int nsplit, const double* c, int k, double shift_rel,
+                               cplx* Rinv, int* fail, double* dev, double dev_fail, const int* skip) {
   const int q = blockIdx.x;
   if (skip && skip[q]) return;
   extern __shared__ __align__(16) unsigned char chol_smem[];
   cplx* A = reinterpret_cast<cplx*>(chol_smem);            // k x k
   cplx* xd = A + (size_t)k * k;                            // [k] diagonal of R^-1
   const double* cq = c + (size_t)q * k;
-  const cplx* g = G + (size_t)q * k * k;
   __shared__ int bad;
   __shared__ double s_inv;
   __shared__ double s_dev[32];
   int live = 0;
   for (int j = 0; j < k; ++j) live += cq[j] > 0.0;
   const double shift = shift_rel * live;
-  double mydev = 0.0;
+  double mydev = 0.0;                                       // max |G - I|^2 over the live block
   for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) {
     const int i = idx / k, j = idx % k;
     const bool li = cq[i] > 0.0, lj = cq[j] > 0.0;
     cplx v;
     if (li && lj) {
-      v = g[idx];
-      mydev = fmax(mydev, sqrt(cabs2(csub(v, cmk(i == j ? 1.0 : 0.0, 0.0)))));
+      // G = sum of the split-K partial products, added in split order
+      v = cmk(0.0, 0.0);
+      for (int p = 0; p < nsplit; ++p) v = cadd(v, P[((size_t)q * nsplit + p) * k * k + idx]);
+      mydev = fmax(mydev, cabs2(csub(v, cmk(i == j ? 1.0 : 0.0, 0.0))));
       if (i == j) v = cmk(v.x + shift, 0.0);
     } else {
       v = cmk(i == j ? 1.0 : 0.0, 0.0);
@@ -143,20 +160,23 @@ __global__ void cholinv_kernel(const cplx* G, const double* c, int k, double shi
   if (threadIdx.x == 0) {
     double m = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, s_dev[w]);
+    m = sqrt(m);
     dev[q] = m;
     if (dev_fail > 0.0 && !(m <= dev_fail)) bad = 1;
   }
   __syncthreads();
-  // right-looking Cholesky: row j of R, then the rank-1 update of the trailing upper triangle
+  // right-looking Cholesky: row j of R, then the rank-1 update of the trailing upper triangle; the
+  // pivot reciprocals 1 / R_jj are kept in xd[j].y for the back substitution
   for (int j = 0; j < k && !bad; ++j) {
     if (threadIdx.x == 0) {
       const double d = A[(size_t)j * k + j].x;
       if (!(d > 0.0) || !isfinite(d)) {
         bad = 1;
       } else {
-        const double piv = sqrt(d);
-        A[(size_t)j * k + j] = cmk(piv, 0.0);
-        s_inv = 1.0 / piv;
+        const double inv = rsqrt_nr(d);
+        A[(size_t)j * k + j] = cmk(d * inv, 0.0);
+        s_inv = inv;
+        xd[j] = cmk(0.0, inv);
       }
     }
     __syncthreads();
@@ -185,11 +205,11 @@ __global__ void cholinv_kernel(const cplx* G, const double* c, int k, double shi
   // kept at A[l][i], X_ii in xd[i].
   for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x)
     if (idx / k > idx % k) A[idx] = cmk(0.0, 0.0);
-  for (int j = threadIdx.x; j < k; j += blockDim.x) xd[j] = cmk(1.0, 0.0);
   __syncthreads();
   for (int j = k - 1; j >= 0; --j) {
-    const double rinv = 1.0 / A[(size_t)j * k + j].x;
-    if (threadIdx.x == 0) xd[j] = cscale(xd[j], rinv);
+    const double rinv = xd[j].y;                             // 1 / R_jj from the factorisation
+    __syncthreads();
+    if (threadIdx.x == 0) xd[j] = cmk(rinv, 0.0);            // X_jj = 1 / R_jj
     for (int l = j + 1 + threadIdx.x; l < k; l += blockDim.x) A[(size_t)l * k + j] = cscale(A[(size_t)l * k + j], rinv);
     __syncthreads();
     const int w = k - j;
@@ -224,7 +244,6 @@ size_t orth_work_bytes(int N, int k, int batch) {
   add((size_t)batch * N * k * sizeof(cplx));            // ping-pong block
   add((size_t)batch * k * sizeof(double));              // column norms
   add((size_t)batch * nsplit * k * k * sizeof(cplx));   // split-K partials
-  add((size_t)batch * k * k * sizeof(cplx));            // Gram
   add((size_t)batch * k * k * sizeof(cplx));            // R^-1
   add((size_t)batch * sizeof(double));                  // deviation from orthonormality
   return b;
@@ -255,7 +274,6 @@ int orth_cqr(const OrthDesc& d, cudaStream_t st) {
   cplx* Xt = (cplx*)take((size_t)B * N * k * sizeof(cplx));
   double* c = (double*)take((size_t)B * k * sizeof(double));
   cplx* part = (cplx*)take((size_t)B * nsplit * k * k * sizeof(cplx));
-  cplx* G = (cplx*)take((size_t)B * k * k * sizeof(cplx));
   cplx* Rinv = (cplx*)take((size_t)B * k * k * sizeof(cplx));
   double* dev = (double*)take((size_t)B * sizeof(double));
   if ((size_t)(w - (char*)d.work) > d.work_bytes) return cuda_fail(cudaErrorInvalidValue, "orth workspace", __FILE__, __LINE__);
@@ -269,14 +287,17 @@ int orth_cqr(const OrthDesc& d, cudaStream_t st) {
   // passes: shifted, plain, plain; Xh -> Xt -> Xh -> Q
   const double shift = 11.0 * ((double)N * k + (double)k * (k + 1)) * 1.1102230246251565e-16;
   cplx* src = Xh;
+  const int tiles = (k + GT - 1) / GT;
   for (int pass = 0; pass < d.passes; ++pass) {
-    if (int rc = atb_product(src, (long long)N * k, src, (long long)N * k, N, k, B, part, G, (long long)k * k,
-                             d.skip, st))
-      return rc;
+    IPEPS_LAUNCH(K_ORTH, 8.0 * B * (double)N * k * k, st,
+                 atb_partial_kernel<<<dim3(tiles, tiles, B * nsplit), GT * GT, 0, st>>>(src, (long long)N * k, src,
+                                                                                      (long long)N * k, N, k,
+                                                                                      nsplit, part, d.skip));
+    const bool shifted = d.shifted && pass == 0;
     IPEPS_LAUNCH(K_ORTH, 0, st,
-                 cholinv_kernel<<<B, 256, orth_smem_bytes(k), st>>>(G, c, k, pass == 0 ? shift : 0.0, Rinv, d.fail,
-                                                                   dev, pass + 1 == d.passes ? d.dev_fail : 0.0,
-                                                                   d.skip));
+                 cholinv_kernel<<<B, 256, orth_smem_bytes(k), st>>>(part, nsplit, c, k, shifted ? shift : 0.0, Rinv,
+                                                                   d.fail, dev,
+                                                                   pass + 1 == d.passes ? d.dev_fail : 0.0, d.skip));
     IPEPS_CUDA_TRY(cudaGetLastError());
     cplx* dst = pass + 1 == d.passes ? d.Q : (src == Xh ? Xt : Xh);
     const long long sD = pass + 1 == d.passes ? d.sQ : (long long)N * k;

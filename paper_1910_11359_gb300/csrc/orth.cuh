@@ -14,7 +14,9 @@ struct OrthDesc {
   int* fail;                     // [batch]: set to 1 (never cleared here) when the factorisation
                                  // broke down or the last pass still saw a Gram matrix off the
                                  // identity by more than dev_fail
-  int passes;                    // Cholesky QR passes: the first shifted, the others plain (>= 2)
+  int passes;                    // Cholesky QR passes (>= 1)
+  bool shifted;                  // the first pass adds the diagonal shift (for blocks that may be
+                                 // far from orthonormal after column scaling; then passes >= 3)
   double dev_fail;
 };
 

@@ -102,6 +102,8 @@ void prof_end(int cls, cudaStream_t st, double flops, cudaEvent_t start) {
   g_recs.push_back({cls, start, e, flops});
 }
 
+bool prof_enabled() { return g_on.load(std::memory_order_relaxed); }
+
 }  // namespace ipeps
 
 using namespace ipeps;

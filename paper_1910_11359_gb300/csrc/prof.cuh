@@ -36,6 +36,9 @@ unsigned long long* prof_device_counters();
 // executed tensor-pipe flops of the tcgen05 GEMM launches (tallied while timing is on)
 void prof_add_tc_executed(double flops);
 
+// whether launches are being timed (convergence graphs are used only when they are not)
+bool prof_enabled();
+
 }  // namespace ipeps
 
 #define IPEPS_LAUNCH(cls, flops, st, ...)                                  \

@@ -15,11 +15,23 @@
 //     finished accumulator; every wait is bounded: on timeout the CTA raises DEV_TIMEOUT in the
 //     error word, the other roles stop, outstanding TMA loads are drained (bounded) and the TMEM
 //     columns are released before the CTA exits.
+//   * TF32 operands (kind::tf32, the TF32x3 split): the tensor cores add each MMA's products into the
+//     FP32 accumulator with a truncating alignment, a bias of order 2^-24 |acc| per MMA that grows
+//     linearly with K (measured: 1e-7 K relative to |a| |b| sqrt(K) with one accumulator, above the
+//     split's own 2^-22).  So each K tile (four MMAs) is accumulated from zero in one of two TMEM
+//     buffers, alternately, and the epilogue warps add the finished tile into FP32 registers with
+//     round-to-nearest while the next tile is multiplied into the other buffer (accfull / accfree
+//     mbarriers per buffer).  The bias is then that of four MMAs per tile; what remains is the
+//     FP32 rounding of the tile sum, ~2^-24 sqrt(number of tiles) (measured 6e-7 .. 3e-6 for K = 32
+//     .. 1200, against 1.4e-5 at K = 162 with one accumulator).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
+#include <cstdlib>
+#include <map>
 #include <mutex>
+#include <tuple>
 
 #include "prof.cuh"
 #include "tc_gemm.cuh"
@@ -43,7 +55,10 @@ template <int OPT> struct OpCfg {
 template <int BN, int OPT> struct TileCfg {
   static constexpr uint32_t B_BYTES = BN * ROW_BYTES;
   static constexpr uint32_t SMEM_BYTES = STAGES * (A_BYTES + B_BYTES) + 1024 + 256;
-  static constexpr uint32_t TMEM_COLS = BN;
+  // TF32: two accumulator buffers of BN columns (per-tile accumulation, BN = 128 only)
+  static_assert(OPT != OP_TF32 || BN == 128, "TF32 tiles are 128 wide");
+  static constexpr bool CHUNKED = OPT == OP_TF32;
+  static constexpr uint32_t TMEM_COLS = CHUNKED ? 2 * BN : BN;
   // instruction descriptor: A and B of the operand type (same for both, K-major), FP32
   // accumulator, M = 128, N = BN
   static constexpr uint32_t IDESC = (1u << 4)                  // D format F32
@@ -76,6 +91,9 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
     if ((it & 255) == 255 && *abort_flag) return false;
   }
   return false;
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
@@ -115,10 +133,13 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   constexpr int BK = OpCfg<OPT>::BK;
   const uint32_t sB = sA + STAGES * A_BYTES;
   unsigned char* tail = smem + STAGES * (A_BYTES + Cfg::B_BYTES);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(tail);       // full[STAGES], empty[STAGES], done
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tail + 8 * (2 * STAGES + 1));
+  // full[STAGES], empty[STAGES], done, accfull[2], accfree[2]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(tail);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tail + 8 * (2 * STAGES + 5));
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * STAGES, done_bar = full0 + 16 * STAGES;
+  const uint32_t accfull0 = done_bar + 8, accfree0 = done_bar + 24;
+  constexpr bool CHUNKED = Cfg::CHUNKED;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM, bz = blockIdx.z;
@@ -129,6 +150,10 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       mbar_init(empty0 + 8 * s, 1);
     }
     mbar_init(done_bar, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(accfull0 + 8 * b, 1);
+      mbar_init(accfree0 + 8 * b, 4);       // one arrival per epilogue warp
+    }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -173,6 +198,14 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     for (int kt = 0; kt < ktiles; ++kt) {
       const int s = kt % STAGES;
       const uint32_t ph = (uint32_t)(kt / STAGES) & 1u;
+      const int buf = CHUNKED ? (kt & 1) : 0;
+      // per-tile accumulation: the buffer's previous tile (kt - 2) has been read by the epilogue
+      if (CHUNKED && kt >= 2 && !mbar_wait(accfree0 + 8 * buf, (uint32_t)((kt - 2) >> 1) & 1u, abort_flag)) {
+        *abort_flag = 1;
+        atomicOr(err, (unsigned)DEV_TIMEOUT);
+        ok = false;
+        break;
+      }
       if (!mbar_wait(full0 + 8 * s, ph, abort_flag)) {
         *abort_flag = 1;
         atomicOr(err, (unsigned)DEV_TIMEOUT);
@@ -183,12 +216,12 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       const uint64_t da = smem_desc(sA + s * A_BYTES), db = smem_desc(sB + s * Cfg::B_BYTES);
 #pragma unroll
       for (int k = 0; k < ROW_BYTES / 32; ++k) {
-        const uint32_t acc = (kt > 0 || k > 0) ? 1u : 0u;
+        const uint32_t acc = (k > 0 || (!CHUNKED && kt > 0)) ? 1u : 0u;
         const uint64_t adv = (uint64_t)((k * 32) >> 4);   // 32 bytes along K per MMA
         if constexpr (OPT == OP_TF32) {
           asm volatile(
               "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-              " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+              " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + (uint32_t)(buf * BN)),
               "l"(da + adv), "l"(db + adv), "r"(Cfg::IDESC), "r"(acc)
               : "memory");
         } else {
@@ -203,12 +236,68 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                        empty0 + 8 * s)
                    : "memory");
+      if (CHUNKED)   // this tile's accumulation is complete
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         accfull0 + 8 * buf)
+                     : "memory");
     }
     (void)ok;
     // accumulator complete (also signalled after an abort, so the epilogue never waits forever)
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                      done_bar)
                  : "memory");
+  } else if (warp >= 2 && CHUNKED) {
+    // ---------------- epilogue, per-tile accumulation: TMEM lanes 32 q .. 32 q + 31 (q = warp % 4);
+    // each thread owns one output row and adds every finished tile into BN registers
+    const int q = warp & 3;
+    float sum[BN];
+#pragma unroll
+    for (int j = 0; j < BN; ++j) sum[j] = 0.0f;
+    bool ok = true;
+    for (int kt = 0; kt < ktiles; ++kt) {
+      const int buf = kt & 1;
+      bool got = mbar_wait(accfull0 + 8 * buf, (uint32_t)(kt >> 1) & 1u, abort_flag);
+      got = __all_sync(0xffffffffu, got && !*abort_flag);
+      if (!got) {
+        if (lane == 0) {
+          *abort_flag = 1;
+          atomicOr(err, (unsigned)DEV_TIMEOUT);
+        }
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        uint32_t r[32];
+        const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * BN + c0);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+            "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+            "%28, %29, %30, %31}, [%32];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+              "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+              "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+              "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+              "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+              "=r"(r[31])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int j = 0; j < 32; ++j) sum[c0 + j] = __fadd_rn(sum[c0 + j], __uint_as_float(r[j]));
+      }
+      // the buffer may be overwritten by tile kt + 2
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(accfree0 + 8 * buf);
+    }
+    if (ok) {
+      float* crow = C + (long long)bz * strideC + (long long)(m0 + 32 * q + lane) * ldc + n0;
+      float4* dst = reinterpret_cast<float4*>(crow);
+#pragma unroll
+      for (int j = 0; j < BN / 4; ++j)
+        dst[j] = make_float4(sum[4 * j], sum[4 * j + 1], sum[4 * j + 2], sum[4 * j + 3]);
+    }
   } else if (warp >= 2) {
     // ---------------- epilogue: TMEM lanes (32 q .. 32 q + 31) of warp quarter q = warp % 4
     const int q = warp & 3;
@@ -433,6 +522,82 @@ static int pick_bn(int M, int N) {
   return (N > 128 && tiles256 >= 152) ? 256 : 128;
 }
 
+// ---- tile-width autotuner.  The output-tile width does not enter the arithmetic (every output is
+// the same K-ordered sum of the same MMA products whatever N the instruction has), so it is picked by
+// timing: the first product of each (M, N, K) shape runs with BN = 128 and 256, three timed
+// launches each after one warm-up, and the faster width serves every later product of that shape,
+// in any batch.  IPEPS_TUNE=0 uses the pick_bn heuristic instead, IPEPS_TUNE=128 or 256 forces that
+// width (tests compare the two); tuning is also skipped while the stream is being captured (the
+// heuristic serves until the shape is tuned) and for products too narrow for a 256 tile.
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, int, int>, int> g_tuned_bn;
+
+static int tune_mode() {     // 1: tune; 0: heuristic; 128 / 256: forced width
+  static const int mode = [] {
+    const char* e = std::getenv("IPEPS_TUNE");
+    if (!e || !e[0]) return 1;
+    const int v = std::atoi(e);
+    return (v == 0 || v == 128 || v == 256) ? v : 1;
+  }();
+  return mode;
+}
+
+int tuned_tile_width(int M, int N, int K) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tuned_bn.find(std::make_tuple(M, N, K));
+  return it == g_tuned_bn.end() ? 0 : it->second;
+}
+
+template <int OPT>
+static int gemm_raw(const void* A3, const void* B3t, float* C32, int Mp, int Np, int ncols, int Kp, int batch,
+                    int bn, double algo_flops, unsigned* err, cudaStream_t st, const int* skip, int skip_mod);
+
+// returns the tile width for this BF16 product, tuning it on the prepared operands if needed
+static int tile_width(int M, int N, int K, const void* A3, const void* B3, float* C32, int Mp, int Np, int Kp,
+                      int batch, unsigned* err, cudaStream_t st, const int* skip, int skip_mod) {
+  const int heuristic = pick_bn(M, N), mode = tune_mode();
+  if (N <= 128) return 128;
+  if (mode == 128 || mode == 256) return mode;
+  if (mode == 0) return heuristic;
+  const auto key = std::make_tuple(M, N, K);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned_bn.find(key);
+    if (it != g_tuned_bn.end()) return it->second;
+  }
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return heuristic;
+  }
+  cudaEvent_t e0, e1;
+  IPEPS_CUDA_TRY(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cuda_fail(cudaGetLastError(), "tune events", __FILE__, __LINE__);
+  }
+  float best_ms = 0.0f;
+  int best = heuristic, rc = 0;
+  for (int bn : {128, 256}) {
+    float ms = 0.0f;
+    rc = gemm_raw<OP_BF16>(A3, B3, C32, Mp, Np, N, Kp, batch, bn, -1.0, err, st, skip, skip_mod);
+    if (!rc && cudaEventRecord(e0, st) != cudaSuccess) rc = cuda_fail(cudaGetLastError(), "tune", __FILE__, __LINE__);
+    for (int r = 0; r < 3 && !rc; ++r)
+      rc = gemm_raw<OP_BF16>(A3, B3, C32, Mp, Np, N, Kp, batch, bn, -1.0, err, st, skip, skip_mod);
+    if (!rc && (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+      rc = cuda_fail(cudaGetLastError(), "tune timing", __FILE__, __LINE__);
+    if (rc) break;
+    if (bn == 128 || ms < best_ms) { best_ms = ms; best = bn; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return -rc;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tuned_bn[key] = best;
+  return best;
+}
+
 static int k_tile(int op) { return op == SPLIT_TF32 ? OpCfg<OP_TF32>::BK : OpCfg<OP_BF16>::BK; }
 static int elem_bytes(int op) { return op == SPLIT_TF32 ? 4 : 2; }
 
@@ -442,8 +607,8 @@ size_t split_workspace_bytes(int M, int N, int K, int batch, int op) {
 }
 
 template <int BN, int OPT>
-static int launch_tc(const CUtensorMap& mA, const CUtensorMap& mB, float* C32, int Mp, int Np, int Kp,
-                     int batch, double algo_flops, unsigned* err, const int* skip, int skip_mod,
+static int launch_tc(const CUtensorMap& mA, const CUtensorMap& mB, float* C32, int Mp, int Np, int ncols,
+                     int Kp, int batch, double algo_flops, unsigned* err, const int* skip, int skip_mod,
                      cudaStream_t st) {
   using Cfg = TileCfg<BN, OPT>;
   static std::once_flag once;
@@ -453,8 +618,9 @@ static int launch_tc(const CUtensorMap& mA, const CUtensorMap& mB, float* C32, i
                                     (int)Cfg::SMEM_BYTES);
   });
   IPEPS_CUDA_TRY(attr_err);
-  dim3 grid(Np / BN, Mp / BM, batch);
-  const double flops = 2.0 * Mp * (double)Np * Kp * batch;     // executed on the tensor pipe
+  // output tiles over the first ncols columns (C32 rows are Np >= round_up(ncols, BN) wide)
+  dim3 grid((ncols + BN - 1) / BN, Mp / BM, batch);
+  const double flops = 2.0 * Mp * (double)grid.x * BN * Kp * batch;     // executed on the tensor pipe
   prof_add_tc_executed(flops);
   IPEPS_LAUNCH(K_TC_GEMM, algo_flops > 0.0 ? algo_flops : flops, st,
                (tc_gemm_kernel<BN, OPT><<<grid, THREADS, Cfg::SMEM_BYTES, st>>>(
@@ -464,30 +630,38 @@ static int launch_tc(const CUtensorMap& mA, const CUtensorMap& mB, float* C32, i
 }
 
 template <int OPT>
-static int gemm_raw(const void* A3, const void* B3t, float* C32, int Mp, int Np, int Kp, int batch, int bn,
-                    double algo_flops, unsigned* err, cudaStream_t st, const int* skip, int skip_mod) {
-  if ((bn != 128 && bn != 256) || Mp % BM || Np % bn || Kp % OpCfg<OPT>::BK || batch < 1 || batch > 65535)
+static int gemm_raw(const void* A3, const void* B3t, float* C32, int Mp, int Np, int ncols, int Kp, int batch,
+                    int bn, double algo_flops, unsigned* err, cudaStream_t st, const int* skip, int skip_mod) {
+  if ((bn != 128 && bn != 256) || Mp % BM || Np % 128 || ncols < 1 || round_up(ncols, bn) > Np ||
+      Kp % OpCfg<OPT>::BK || batch < 1 || batch > 65535)
     return cuda_fail(cudaErrorInvalidValue, "tc gemm shape", __FILE__, __LINE__);
   if (((uintptr_t)A3 & 15) || ((uintptr_t)B3t & 15) || ((uintptr_t)C32 & 15))
     return cuda_fail(cudaErrorInvalidValue, "tc gemm alignment", __FILE__, __LINE__);
   CUtensorMap mA, mB;
   if (int rc = make_map<OPT>(&mA, A3, Mp, Kp, batch, BM)) return rc;
   if (int rc = make_map<OPT>(&mB, B3t, Np, Kp, batch, bn)) return rc;
-  return bn == 256 ? launch_tc<256, OPT>(mA, mB, C32, Mp, Np, Kp, batch, algo_flops, err, skip, skip_mod, st)
-                   : launch_tc<128, OPT>(mA, mB, C32, Mp, Np, Kp, batch, algo_flops, err, skip, skip_mod, st);
+  if constexpr (OPT == OP_TF32) {
+    if (bn != 128) return cuda_fail(cudaErrorInvalidValue, "tc gemm tf32 tile width", __FILE__, __LINE__);
+    return launch_tc<128, OPT>(mA, mB, C32, Mp, Np, ncols, Kp, batch, algo_flops, err, skip, skip_mod, st);
+  } else {
+    return bn == 256
+               ? launch_tc<256, OPT>(mA, mB, C32, Mp, Np, ncols, Kp, batch, algo_flops, err, skip, skip_mod, st)
+               : launch_tc<128, OPT>(mA, mB, C32, Mp, Np, ncols, Kp, batch, algo_flops, err, skip, skip_mod, st);
+  }
 }
 
 int gemm_bf16_raw(const void* A3, const void* B3t, float* C32, int Mp, int Np, int Kp, int batch,
                   int bn, double algo_flops, unsigned* err, cudaStream_t st, const int* skip,
                   int skip_mod) {
-  return gemm_raw<OP_BF16>(A3, B3t, C32, Mp, Np, Kp, batch, bn, algo_flops, err, st, skip, skip_mod);
+  return gemm_raw<OP_BF16>(A3, B3t, C32, Mp, Np, Np, Kp, batch, bn, algo_flops, err, st, skip, skip_mod);
 }
 
 template <typename T, int OPT>
 static int zgemm_split_t(const GemmDesc& g, void* work, size_t work_bytes, unsigned* err, cudaStream_t st) {
   const int op = OPT == OP_TF32 ? SPLIT_TF32 : SPLIT_BF16;
-  const int bn = pick_bn(g.M, g.N);
-  const int Mp = round_up(2 * g.M, BM), Np = round_up(g.N, bn), Kp = round_up(6 * g.K, OpCfg<OPT>::BK);
+  // operand / product layout: rows of B3 and C32 padded to 256 when a 256-wide tile may be used
+  const int Mp = round_up(2 * g.M, BM), Kp = round_up(6 * g.K, OpCfg<OPT>::BK);
+  const int Np = (OPT == OP_BF16 && g.N > 128) ? round_up(g.N, 256) : round_up(g.N, 128);
   if (split_workspace_bytes(g.M, g.N, g.K, g.batch, op) > work_bytes)
     return cuda_fail(cudaErrorInvalidValue, "split workspace too small", __FILE__, __LINE__);
   char* w = (char*)(((uintptr_t)work + 1023) & ~(uintptr_t)1023);
@@ -510,7 +684,12 @@ static int zgemm_split_t(const GemmDesc& g, void* work, size_t work_bytes, unsig
   IPEPS_LAUNCH(K_TC_PREP, 0, st, prep_b_kernel<T><<<pb, pblk, 0, st>>>(g, B3, Np, Kp));
   IPEPS_CUDA_TRY(cudaGetLastError());
   const double algo = 8.0 * g.M * (double)g.N * g.K * g.batch;   // the complex product's own flops
-  if (int rc = gemm_raw<OPT>(A3, B3, C32, Mp, Np, Kp, g.batch, bn, algo, err, st, g.skip, g.skip_mod)) return rc;
+  int bn = 128;
+  if constexpr (OPT == OP_BF16) {
+    bn = tile_width(g.M, g.N, g.K, A3, B3, C32, Mp, Np, Kp, g.batch, err, st, g.skip, g.skip_mod);
+    if (bn < 0) return -bn;
+  }
+  if (int rc = gemm_raw<OPT>(A3, B3, C32, Mp, Np, g.N, Kp, g.batch, bn, algo, err, st, g.skip, g.skip_mod)) return rc;
   const dim3 gc((g.N + 255) / 256, g.M, g.batch);
   IPEPS_LAUNCH(K_TC_PREP, 0, st, gather_c_kernel<<<gc, 256, 0, st>>>(g, C32, Mp, Np));
   IPEPS_CUDA_TRY(cudaGetLastError());

@@ -19,5 +19,7 @@ int zgemm_split(const GemmDesc& g, int op, void* work, size_t work_bytes, unsign
 int gemm_bf16_raw(const void* A3, const void* B3t, float* C32, int Mp, int Np, int Kp, int batch,
                   int bn, double algo_flops, unsigned* err, cudaStream_t st, const int* skip = nullptr,
                   int skip_mod = 0);
+// tile width the autotuner chose for BF16 products of this shape (0: not tuned yet)
+int tuned_tile_width(int M, int N, int K);
 }  // namespace tc
 }  // namespace ipeps

@@ -172,7 +172,8 @@ def unique_row(row, keys):
     """Whether the oracle shows a row's readout to be a unique result of the method: warm and cold
     readouts both converged to the tolerance (not stopped by the stall rule or the sweep cap), agree
     within UNIQUE_TOL, survive the stability probe (a relative 1e-6 kick of the converged
-    environment converges back within UNIQUE_TOL), no multiplet decision at the chi cut was within
+    environment converges back within UNIQUE_TOL, and so does a relative 1e-4 kick: a second fixed
+    point that close is one a warm start from a slightly different trajectory can reach), no multiplet decision at the chi cut was within
     two decades of its threshold or dropped a multiplet above 1e-7 of the largest value (C8), and
     FP64 arithmetic determines the readout to a tenth of UNIQUE_TOL (a rounding-level kick of the site
     tensors moves the re-converged readout by less than that: the oracle's sensitivity probe).
@@ -185,6 +186,9 @@ def unique_row(row, keys):
         return False, "warm-cold %.0e" % d
     if max(row["drift"], c["drift"]) >= UNIQUE_TOL:
         return False, "unstable %.0e" % max(row["drift"], c["drift"])
+    wide = max(row.get("drift_split", np.inf), c.get("drift_split", np.inf))
+    if wide >= UNIQUE_TOL:
+        return False, "second fixed point %.0e" % wide
     if min(row["c8_margin"], c["c8_margin"]) < 2.0 or max(row["c8_level"], c["c8_level"]) > 1e-7:
         return False, "C8"
     sens = max(row.get("sensitivity", np.inf), c.get("sensitivity", np.inf))

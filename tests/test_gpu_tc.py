@@ -107,10 +107,15 @@ def test_split_ctmrg_random_d4_vs_fp64():
 
 @pytest.mark.parametrize("M,N,K,batch,opA,opB", [(64, 128, 32, 1, 0, 0), (162, 162, 162, 3, 0, 0),
                                                  (75, 131, 51, 2, 2, 0), (1024, 520, 40, 4, 0, 0),
-                                                 (1500, 700, 70, 3, 1, 2)])
+                                                 (1500, 700, 70, 3, 1, 2), (96, 200, 1200, 1, 0, 0)])
 def test_split_gemm_tf32_matches_fp64(M, N, K, batch, opA, opB):
-    """TF32x3 (kind::tf32): two TF32 terms per value, three products, FP32 accumulation: about 64x
-    more accurate than the BF16x3 split (relative error ~3e-7 of |a| |b| sqrt(K))."""
+    """TF32x3 (kind::tf32): two TF32 terms per value, three products.  The tensor cores' truncating
+    accumulation biases each MMA by ~2^-24 of the accumulator; with one accumulator over all of K
+    that bias grew like 1e-7 K relative to |a| |b| sqrt(K) (1.4e-5 at K = 162).  Accumulating each
+    K tile of four MMAs separately and summing the tiles in FP32 (round to nearest) leaves the
+    tiles' own bias and the summation's rounding, ~2^-24 sqrt(number of tiles) of the result:
+    measured 6e-7 (K = 32) to 3e-6 (K = 1200, 225 tiles) as the largest error over all outputs, a
+    tenth of the BF16x3 split's."""
     import paper_1910_11359_gb300 as pkg
     rng = np.random.default_rng(9)
     A = rng.standard_normal((batch,) + ((M, K) if opA == 0 else (K, M))) \
@@ -129,7 +134,7 @@ def test_split_gemm_tf32_matches_fp64(M, N, K, batch, opA, opB):
     scale = np.sqrt(K) * np.sqrt(np.mean(np.abs(A) ** 2)) * np.sqrt(np.mean(np.abs(B) ** 2))
     err = np.max(np.abs(C - ref)) / scale
     print("TF32x3 split GEMM relative error %.2e" % err)
-    assert err < 3e-6
+    assert err < 5e-6
     assert err > 1e-12
 
 
@@ -152,3 +157,36 @@ def test_tf32x3_ctmrg_matches_oracle_d3():
     err = max(abs(obs[k] - ref[k]) for k in ("nA", "nB", "imbalance", "energy"))
     print("TF32x3 CTMRG vs FP64 oracle: observables %.1e" % err)
     assert err < 1e-6 and err > 1e-14
+
+
+def test_tile_width_leaves_results_unchanged(tmp_path):
+    """The autotuner picks the tcgen05 output-tile width (128 or 256 columns) by timing; the width
+    must not enter the arithmetic.  The same BF16x3 product computed with each width forced
+    (IPEPS_TUNE=128 / 256, separate processes) is identical bit for bit."""
+    import os
+    import subprocess
+    import sys
+    code = """
+import ctypes, sys
+import numpy as np, torch
+sys.path.insert(0, %r)
+import paper_1910_11359_gb300 as pkg
+rng = np.random.default_rng(5)
+M, N, K, batch = 300, 700, 90, 2
+A = rng.standard_normal((batch, M, K)) + 1j * rng.standard_normal((batch, M, K))
+B = rng.standard_normal((batch, K, N)) + 1j * rng.standard_normal((batch, K, N))
+dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+dC = torch.zeros((batch, M, N), dtype=torch.complex128, device="cuda")
+p = lambda t: ctypes.c_void_p(t.data_ptr())
+rc = pkg.lib().ipeps_kernel_zgemm_split(M, N, K, batch, 0, 0, p(dA), K, M * K, p(dB), N, K * N, p(dC), N,
+                                        M * N, None)
+assert rc == 0
+np.save(sys.argv[1], dC.cpu().numpy())
+""" % os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = {}
+    for bn in ("128", "256"):
+        f = str(tmp_path / ("c%s.npy" % bn))
+        env = dict(os.environ, IPEPS_TUNE=bn)
+        subprocess.run([sys.executable, "-c", code, f], check=True, env=env, timeout=300)
+        out[bn] = np.load(f)
+    assert np.array_equal(out["128"], out["256"])
