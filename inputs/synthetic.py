@@ -70,3 +70,22 @@ def random_site_tensors(d, D, seed, product_weight=1.0, noise=0.3):
         t[:, 0, 0, 0, 0] += product_weight * v / np.linalg.norm(v)
         out.append(t)
     return out[0], out[1]
+
+
+# Free-fermion exact-diagonalisation workload (paper Sec. "Set up for non-interacting fermions";
+# Fig. 2-4): L x L lattices, 100 disorder realisations, h in {4, 10, 100}, continuous disorder or a
+# three-level (spin-1) discrete one, Neel start, particle numbers on even / odd sites for t in
+# [0, 5] (a few tunnelling times), inverse participation ratios binned over the rescaled spectrum.
+ED = dict(Ls=(10, 20, 40), R=100, hs=(4.0, 10.0, 100.0), levels=3, J=1.0,
+          times=tuple(0.1 * k for k in range(51)), bin_width=0.05)
+
+
+def ed_fields(L, R, h, levels, seed):
+    """On-site fields [R][L*L] of R disorder realisations (numpy default_rng(seed)): continuous
+    (levels = 0) uniform in [-h, h]; discrete, `levels` values -h + 2 h k / (levels - 1) drawn with
+    equal probability."""
+    rng = np.random.default_rng(seed)
+    if levels == 0:
+        return rng.uniform(-h, h, size=(R, L * L))
+    k = rng.integers(0, levels, size=(R, L * L))
+    return -h + 2.0 * h * k / (levels - 1)
