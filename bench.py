@@ -54,11 +54,17 @@ def parse():
     ap.add_argument("--impl", choices=("native", "reference"), default="native")
     ap.add_argument("--contraction-D", type=int, default=6,
                     help="bond dimension of the contraction sub-benchmark in the default line (0: skip)")
-    ap.add_argument("--requests", type=int, default=32, help="serve workload: requests in the stream")
-    ap.add_argument("--workload", choices=("quench", "ctmrg", "sweep", "serve"), default="quench",
+    ap.add_argument("--requests", type=int, default=400, help="serve workload: requests in the stream")
+    ap.add_argument("--serve-seconds", type=float, default=240.0,
+                    help="serve workload: window served per precision (seconds)")
+    ap.add_argument("--serve-one", action="store_true",
+                    help="serve workload: serve one window at --precision in this process and print its "
+                         "summary (the parent runs one such process per precision)")
+    ap.add_argument("--workload", choices=("quench", "ctmrg", "sweep", "serve", "ed"), default="quench",
                     help="quench: the Trotter+CTMRG readout workload (default); ctmrg: the standalone "
                          "CTMRG contraction benchmark on random tensors; sweep: the batched "
-                         "64-instance disorder sweep")
+                         "64-instance disorder sweep; serve: the request stream; ed: the free-fermion "
+                         "exact-diagonalisation workload")
     ap.add_argument("--sequential", action="store_true",
                     help="sweep workload: run the (D, chi) groups one after the other")
     ap.add_argument("--D", type=int, default=4, help="ctmrg workload: bond dimension (chi = 2 D^2)")
@@ -421,7 +427,12 @@ def native_main(args):
                                "(value itself is timed with the per-launch events off)" % nprof},
         "kernel_time_share": shares,
         "latency_ms": latency_summary(step_ms, sweep_ms),
-        "gpu_launches": int(launches),
+        # the timed pass runs each convergence as one CUDA graph, whose kernels the host does not
+        # launch one by one: count kernel executions from the host-loop (profiled) pass instead
+        "gpu_launches": int(round(sum(v[2] for v in prof.values()) * args.steps / max(1, nprof))),
+        "gpu_launches_note": "kernel executions, counted per launch in the host-loop profiled pass and "
+                             "scaled to the timed steps (the timed pass itself issued %d host launches "
+                             "and graph launches)" % int(launches),
         "clocks": clk,
         "cpu_baseline": {"value": STEPS_PER_READOUT / full["total"], "unit": UNIT, "cores": 1,
                          "kind": "oracle", "sample": ORACLE_SAMPLE,
@@ -539,8 +550,7 @@ def ctmrg_main(args):
             sim.ctmrg_reset()
             sim.ctmrg_converge(tol=0.0, max_sweeps=sweeps)
         torch.cuda.synchronize()
-        pkg.profile_enable(True)
-        launches0 = pkg.launch_count()
+        # timed with the per-launch events off (each convergence after its first sweep is one graph)
         total = 0.0
         for _ in range(args.steps):
             sim.ctmrg_reset()
@@ -551,10 +561,16 @@ def ctmrg_main(args):
             e1.record(stream)
             e1.synchronize()
             total += e0.elapsed_time(e1)
+        obs = sim.measure()[0]
+        # profiled pass of one step (host loop, per-launch events): kernel shares, roofline, launches
+        sim.ctmrg_reset()
+        pkg.profile_enable(True)
+        launches0 = pkg.launch_count()
+        sim.ctmrg_converge(tol=0.0, max_sweeps=sweeps)
         prof = pkg.profile_read()
         pkg.profile_enable(False)
-        launches = pkg.launch_count() - launches0
-        obs = sim.measure()[0]
+        launches = (pkg.launch_count() - launches0) * args.steps
+        prof_total = sum(v[0] for v in prof.values())
     sim.close()
     flops = contraction_flops_per_sweep(D, chi) * sweeps * args.steps
     dom = max(prof.items(), key=lambda kv: kv[1][0])
@@ -582,36 +598,51 @@ def ctmrg_main(args):
                 "executed_tflops": tc_fl / (tc_ms * 1e-3) / 1e12, "peak": bf16_peak,
                 "frac": tc_fl / (tc_ms * 1e-3) / 1e12 / bf16_peak,
                 "peak_source": "MEASURED_PEAKS.json bf16 burst" if peaks else "fallback"},
-            "kernel_time_share": {k: round(v[0] / total, 4) for k, v in
+            "kernel_time_share": {k: round(v[0] / prof_total, 4) for k, v in
                                   sorted(prof.items(), key=lambda kv: -kv[1][0]) if v[0] > 0},
-            "gpu_launches": int(launches), "imbalance_after": obs["imbalance"]}
+            "gpu_launches": int(launches),
+            "gpu_launches_note": "kernel executions of one step counted in a host-loop pass, times steps",
+            "imbalance_after": obs["imbalance"]}
     print(json.dumps(line))
     return 0
 
 
-def sweep_main(args):
-    """Batched disorder sweep (64 instances of mixed D, one handle per (D, chi) group, groups on
-    concurrent streams): `steps` readout intervals of 0.5 from t = 0, wall-clock timed."""
+def _sweep_run(prec, args, pts, conc):
     import torch
-    from inputs import DISORDER_SWEEP, disorder_sweep_points
-    from paper_1910_11359_gb300.sweep import disorder_sweep, group_points
+    from inputs import DISORDER_SWEEP
+    from paper_1910_11359_gb300.sweep import disorder_sweep
     import paper_1910_11359_gb300 as pkg
-    prec = pkg.SPLIT_BF16X3 if args.precision == "split" else pkg.FP64
-    pts = disorder_sweep_points(DISORDER_SWEEP["n"])
-    conc = not args.sequential
+    kw = dict(dt=DISORDER_SWEEP["dt"], order=DISORDER_SWEEP["order"], precision=prec, concurrent=conc)
     for _ in range(args.warmup):                      # handles, t = 0 readout
-        disorder_sweep(pts, 0.0, DISORDER_SWEEP["meas_every"], dt=DISORDER_SWEEP["dt"], order=DISORDER_SWEEP["order"],
-                       precision=prec, concurrent=conc)
+        disorder_sweep(pts, 0.0, DISORDER_SWEEP["meas_every"], **kw)
     torch.cuda.synchronize()
     launches0 = pkg.launch_count()
     t_max = DISORDER_SWEEP["meas_every"] * args.steps
     t0 = time.perf_counter()
-    out = disorder_sweep(pts, t_max, DISORDER_SWEEP["meas_every"], dt=DISORDER_SWEEP["dt"], order=DISORDER_SWEEP["order"],
-                         precision=prec, concurrent=conc)
+    out = disorder_sweep(pts, t_max, DISORDER_SWEEP["meas_every"], **kw)
     torch.cuda.synchronize()
     sec = time.perf_counter() - t0
-    launches = pkg.launch_count() - launches0
+    return out, sec, t_max, pkg.launch_count() - launches0
+
+
+def sweep_main(args):
+    """Batched disorder sweep (64 instances of mixed D, one handle per (D, chi) group, groups on
+    concurrent streams): `steps` readout intervals of 0.5 from t = 0, wall-clock timed, at the
+    requested precision and then at the other one (split BF16x3 / FP64), with the largest imbalance
+    difference between the two over every instance and readout."""
+    from inputs import DISORDER_SWEEP, disorder_sweep_points
+    from paper_1910_11359_gb300.sweep import group_points
+    import paper_1910_11359_gb300 as pkg
+    prec = pkg.SPLIT_BF16X3 if args.precision == "split" else pkg.FP64
+    other = pkg.FP64 if prec != pkg.FP64 else pkg.SPLIT_BF16X3
+    pts = disorder_sweep_points(DISORDER_SWEEP["n"])
+    conc = not args.sequential
+    out, sec, t_max, launches = _sweep_run(prec, args, pts, conc)
+    out2, sec2, _, _ = _sweep_run(other, args, pts, conc)
+    diff = max(abs(a["imbalance"] - b["imbalance"]) for o1, o2 in zip(out, out2) for a, b in zip(o1, o2))
     steps_total = len(pts) * round(t_max / DISORDER_SWEEP["dt"])
+    pph = lambda s: len(pts) * 3600.0 / (s * DISORDER_SWEEP["t_max"] / t_max)
+    name = lambda p: "split_bf16x3" if p else "fp64"
     line = {"metric": "instance Trotter steps/s", "value": steps_total / sec, "unit": "Trotter steps/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -621,43 +652,139 @@ def sweep_main(args):
                                    "readout every 0.5 (timed from t = 0 to t = %.1f)" % t_max,
                        "groups": {"D=%d chi=%d" % k: len(v) for k, v in group_points(pts).items()},
                        "concurrent_groups": conc, "timing": "wall clock around the whole sweep"},
-            "sweep_points_per_hour": len(pts) * 3600.0 / (sec * DISORDER_SWEEP["t_max"] / t_max),
+            "sweep_points_per_hour": {name(prec): pph(sec), name(other): pph(sec2)},
+            "seconds": {name(prec): sec, name(other): sec2},
+            "max_imbalance_difference_split_vs_fp64": diff,
             "gpu_launches": int(launches),
             "imbalance_last": [round(o[-1]["imbalance"], 6) for o in out[:4]]}
     print(json.dumps(line))
     return 0
 
 
-def serve_main(args):
-    """Serving loop: a seeded Poisson stream of quench requests (mean 4 per second, D in 2..4,
-    chi in [D^2, 3 D^2], h in [0.5, 16], V in {0, 0.5, 1}, t_max in {1, 2}, readouts every 0.5),
-    admitted by footprint under half of the free device memory, run on 4 worker streams."""
+def _serve_run(prec, args):
+    """One bounded window of the request stream at the given precision (run in a process of its
+    own: a worker may still be inside a long library call when the window ends)."""
     import torch
     from paper_1910_11359_gb300.serve import LibraryEngine, Server, percentile, poisson_requests
     import paper_1910_11359_gb300 as pkg
-    prec = pkg.SPLIT_BF16X3 if args.precision == "split" else pkg.FP64
-    reqs = poisson_requests(args.requests, rate=4.0, seed=5, d_choices=(2, 3, 4),
-                            t_max_choices=(1.0, 2.0), precision=prec)
+    reqs = poisson_requests(args.requests, rate=4.0, seed=5, d_choices=(2, 3, 4, 5, 6),
+                            t_max_choices=(2.0, 4.0, 8.0), precision=prec)
     free, _ = torch.cuda.mem_get_info()
     srv = Server(LibraryEngine(tol=1e-10 if prec == pkg.FP64 else 1e-7), budget_bytes=free // 2,
                  workers=4)
     launches0 = pkg.launch_count()
     t0 = time.perf_counter()
-    out = srv.run(reqs)
-    torch.cuda.synchronize()
+    out = srv.run(reqs, deadline=args.serve_seconds)
     sec = time.perf_counter() - t0
+    per = lambda r: int(round(r.meas_every / r.dt))
+    steps = sum(per(r) * max(0, len(r.readouts) - 1) for r in out + srv.unfinished)
     lat = [r.latency for r in out]
-    steps = sum(int(round(r.t_max / r.dt)) for r in out)
-    line = {"metric": "served Trotter steps/s", "value": steps / sec, "unit": "Trotter steps/s",
-            "n_gpus": 1, "steps": len(out), "warmup": 0, "ms_per_step": 1e3 * sec / len(out),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "bf16x3" if prec else "f64", "data": "synthetic",
-            "config": {"workload": "serving loop, %d Poisson requests (mean 4/s), D in 2..4, "
-                                   "chi in [D^2, 3 D^2], t_max in {1, 2}" % len(out),
-                       "budget_bytes": srv.budget, "peak_admitted_bytes": srv.peak_used,
-                       "workers": srv.nworkers, "timing": "wall clock over the whole stream"},
-            "latency_s": {"p50": percentile(lat, 50), "p99": percentile(lat, 99)},
+    arrived = sum(1 for r in reqs if r.arrival <= sec)
+    by_d = {}
+    for r in out:
+        by_d.setdefault(r.D, []).append(r.latency)
+    return {"steps_per_s": steps / sec, "seconds": sec, "trotter_steps": steps, "arrived": arrived,
+            "admitted": len(out) + len(srv.unfinished), "finished": len(out),
+            "unfinished": len(srv.unfinished),
+            "latency_s": {"p50": percentile(lat, 50), "p99": percentile(lat, 99),
+                          "p50_by_D": {str(k): percentile(v, 50) for k, v in sorted(by_d.items())}},
+            "budget_bytes": srv.budget, "peak_admitted_bytes": srv.peak_used,
             "gpu_launches": int(pkg.launch_count() - launches0)}
+
+
+def serve_main(args):
+    """Serving loop on the config-5 stream: seeded Poisson requests (mean 4 per second), D in 2..6,
+    chi in [D^2, 3 D^2], h in [0.5, 16], V in {0, 0.5, 1}, t_max in {2, 4, 8}, readouts every 0.5,
+    admitted by footprint under half of the free device memory and run on 4 worker streams, split
+    precision; then the same stream on the FP64 path.  A D = 6, chi = 108 request alone runs for
+    hours on one GPU, so each precision is served for a bounded window (--serve-seconds), each in a
+    process of its own: the line reports the Trotter steps completed in it (finished and unfinished
+    requests alike), the latency of the requests that finished, and how many arrived, were
+    admitted, finished."""
+    import paper_1910_11359_gb300 as pkg
+    if args.serve_one:
+        prec = pkg.SPLIT_BF16X3 if args.precision == "split" else pkg.FP64
+        print("SERVE " + json.dumps(_serve_run(prec, args)), flush=True)
+        os._exit(0)                      # leave any worker still inside a library call behind
+    runs = {}
+    for prec in (args.precision, "fp64" if args.precision == "split" else "split"):
+        cmd = [sys.executable, os.path.abspath(__file__), "--workload", "serve", "--serve-one", "--precision", prec,
+               "--requests", str(args.requests), "--serve-seconds", str(args.serve_seconds)]
+        out = subprocess.run(cmd, capture_output=True, text=True, timeout=args.serve_seconds + 900)
+        lines = [l for l in out.stdout.splitlines() if l.startswith("SERVE ")]
+        if not lines:
+            raise RuntimeError("serve window at %s failed: %s" % (prec, out.stderr[-2000:]))
+        runs[prec] = json.loads(lines[-1][6:])
+    main = runs[args.precision]
+    other_name = "fp64" if args.precision == "split" else "split"
+    line = {"metric": "served Trotter steps/s", "value": main["steps_per_s"], "unit": "Trotter steps/s",
+            "n_gpus": 1, "steps": main["trotter_steps"], "warmup": 0,
+            "ms_per_step": 1e3 * main["seconds"] / max(1, main["trotter_steps"]),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16x3" if args.precision == "split" else "f64", "data": "synthetic",
+            "config": {"workload": "serving loop, seeded Poisson stream of %d requests (mean 4/s), D in 2..6, "
+                                   "chi in [D^2, 3 D^2], h in [0.5, 16], V in {0, 0.5, 1}, t_max in {2, 4, 8}, "
+                                   "dt = 0.05, readouts every 0.5; served for a %.0f s window per precision"
+                                   % (args.requests, args.serve_seconds),
+                       "workers": 4, "timing": "wall clock over the window"},
+            "served": main, other_name: runs[other_name],
+            "gpu_launches": main["gpu_launches"],
+            "gpu_launches_note": "host launch calls; convergences after their first sweep run as CUDA graphs"}
+    print(json.dumps(line))
+    return 0
+
+
+def ed_main(args):
+    """Free-fermion ED workload: 20 x 20 lattices (the paper's L = 20; its L = 40 exceeds the device
+    eigensolver), 100 realisations, h = 10, continuous disorder and the three-level one, 51 times in
+    [0, 5]; each step is one full ipeps_ed_run (host fields in, host readouts out) per disorder kind.
+    The oracle is timed on a sample of the same workload."""
+    import torch
+    from inputs import ED, ed_fields
+    import paper_1910_11359_gb300 as pkg
+    L, R, h = 20, ED["R"], 10.0
+    times = list(ED["times"])
+    fields = {kind: ed_fields(L, R, h, lv, seed=31 + lv) for kind, lv in (("continuous", 0), ("discrete3", 3))}
+    st = torch.cuda.Stream()
+    for _ in range(args.warmup):
+        for f in fields.values():
+            pkg.ed_run(L, L, 1.0, f, times, stream=st.cuda_stream)
+    torch.cuda.synchronize()
+    launches0 = pkg.launch_count()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for f in fields.values():
+            out = pkg.ed_run(L, L, 1.0, f, times, stream=st.cuda_stream)
+    sec = time.perf_counter() - t0
+    launches = pkg.launch_count() - launches0
+    pkg.profile_enable(True)
+    for f in fields.values():
+        pkg.ed_run(L, L, 1.0, f, times, stream=st.cuda_stream)
+    prof = pkg.profile_read()
+    pkg.profile_enable(False)
+    total = sum(v[0] for v in prof.values())
+    reals = 2 * R * args.steps
+    # the oracle on 4 realisations of the continuous case, one thread (BLAS / LAPACK pinned to 1)
+    code = ("import sys, time; sys.path.insert(0, %r); from inputs import ED, ed_fields; from oracle import ed; "
+            "f = ed_fields(20, 100, 10.0, 0, seed=31)[:4]; t = time.perf_counter(); "
+            "ed.run(20, 20, 1.0, f, list(ED['times'])); print(time.perf_counter() - t)" % ROOT)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    osec = float(subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                                timeout=900).stdout.strip().split()[-1])
+    line = {"metric": "ED realisations/s", "value": reals / sec, "unit": "realisations/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "free-fermion ED, 20x20 open lattice, 100 realisations x {continuous, 3-level} "
+                                   "disorder, h = 10, Neel evolution at 51 times in [0, 5], IPR + cumulative IPR",
+                       "timing": "wall clock around ipeps_ed_run (host buffers in and out, workspace allocated "
+                                 "per call)"},
+            "kernel_time_share": {k: round(v[0] / total, 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])
+                                  if v[0] > 0},
+            "jacobi_sweeps_mean": float(np.mean(out["sweeps"])),
+            "gpu_launches": int(launches),
+            "cpu_baseline": {"value": 4 / osec, "unit": "realisations/s", "cores": 1, "kind": "oracle",
+                             "sample": "4 realisations of the continuous case (numpy eigh + occupations)"},
+            "n_even_last": float(out["n_even"][-1]), "n_odd_last": float(out["n_odd"][-1])}
     print(json.dumps(line))
     return 0
 
@@ -672,6 +799,8 @@ def main():
         return sweep_main(args)
     if args.workload == "serve":
         return serve_main(args)
+    if args.workload == "ed":
+        return ed_main(args)
     return native_main(args)
 
 

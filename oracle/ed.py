@@ -21,7 +21,7 @@ number on the even and on the odd sites (Fig. 2).
 Localisation of the eigenvectors (Eq. IPR): I_k = sum_i |<i|E_k>|^4; the spectrum is rescaled to
 eps_k = (E_k - E_min) / (E_max - E_min) in [0, 1] and the I_k of the states in each interval of
 width 0.05 are summed (the cumulative IPR, Fig. 4), per realisation; realisations are averaged.
-eps = 1 belongs to the last interval.
+There are ceil(1 / width) intervals and eps = 1 belongs to the last one.
 
 Pins (tests/test_oracle_ed.py): J = 0 (site eigenvectors, IPR 1, frozen occupations), the clean
 chain and clean rectangle (closed-form spectrum and IPR), the short-time law
@@ -83,7 +83,7 @@ def ipr(V):
 
 def cumulative_ipr(E, I, width=0.05):
     """Sum of I_k over the states in each interval of the rescaled spectrum (1 / width bins)."""
-    nb = int(round(1.0 / width))
+    nb = int(np.ceil(1.0 / width - 1e-9))          # intervals covering [0, 1]
     span = E[-1] - E[0] if len(E) > 1 else 0.0
     eps = (E - E[0]) / span if span > 0 else np.zeros_like(E)
     b = np.minimum((eps / width).astype(int), nb - 1)

@@ -23,6 +23,11 @@ class IpepsError(RuntimeError):
         self.status = status
 
 
+class EdParams(ctypes.Structure):
+    _fields_ = [("Lx", ctypes.c_int), ("Ly", ctypes.c_int), ("R", ctypes.c_int), ("J", ctypes.c_double),
+                ("T", ctypes.c_int), ("bin_width", ctypes.c_double)]
+
+
 class Params(ctypes.Structure):
     _fields_ = [("batch", ctypes.c_int), ("d_A", ctypes.c_int), ("D", ctypes.c_int),
                 ("chi", ctypes.c_int), ("trotter_order", ctypes.c_int), ("dt", ctypes.c_double),
@@ -50,7 +55,8 @@ EXPORTS = ["ipeps_init", "ipeps_set_tensors", "ipeps_trotter_step", "ctmrg_conve
            "ipeps_profile_enable", "ipeps_profile_classes", "ipeps_profile_name", "ipeps_profile_read",
            "ipeps_kernel_fp64_peak", "ipeps_kernel_svd_noalloc", "ipeps_kernel_zgemm_split",
            "ipeps_get_env", "ipeps_set_env", "ipeps_profile_tc_executed", "ipeps_profile_counters",
-           "ipeps_kernel_orth", "ipeps_kernel_zgemm_split_tf32", "ipeps_set_graphs"]
+           "ipeps_kernel_orth", "ipeps_kernel_zgemm_split_tf32", "ipeps_set_graphs", "ipeps_ed_max_sites",
+           "ipeps_ed_bytes", "ipeps_ed_run"]
 
 
 def lib():
@@ -70,6 +76,9 @@ def lib():
     L.ctmrg_converge.argtypes = [vp, d, i, ip, dp]
     L.ctmrg_reset.argtypes = [vp]
     L.ipeps_set_graphs.argtypes = [vp, i]
+    L.ipeps_ed_max_sites.argtypes = []
+    L.ipeps_ed_bytes.argtypes = [P(EdParams), P(ctypes.c_size_t)]
+    L.ipeps_ed_run.argtypes = [P(EdParams), dp, dp, dp, dp, dp, dp, dp, ip, vp]
     L.ipeps_measure.argtypes = [vp, P(Obs)]
     L.ipeps_corner_spectrum.argtypes = [vp, i, i, i, dp]
     L.ipeps_get_lambda.argtypes = [vp, dp]
@@ -267,3 +276,29 @@ def fp64_peak_tflops():
     out = ctypes.c_double(0.0)
     _check(lib().ipeps_kernel_fp64_peak(ctypes.byref(out)))
     return out.value
+
+
+def ed_max_sites():
+    """Largest lattice (Lx * Ly sites) the free-fermion ED workload accepts."""
+    return lib().ipeps_ed_max_sites()
+
+
+def ed_run(Lx, Ly, J, fields, times, bin_width=0.05, stream=None):
+    """Free-fermion ED of R realisations (fields [R][Lx*Ly]) on the device: realisation-averaged
+    even / odd occupations at `times`, averaged cumulative IPR, spectra and IPRs per realisation,
+    Jacobi sweeps per realisation (include/ipeps_ed.h)."""
+    f = np.ascontiguousarray(np.atleast_2d(fields), dtype=np.float64)
+    t = np.ascontiguousarray(times, dtype=np.float64)
+    R, N = f.shape
+    if N != Lx * Ly:
+        raise ValueError("fields must have Lx * Ly columns")
+    p = EdParams(Lx=Lx, Ly=Ly, R=R, J=J, T=len(t), bin_width=bin_width)
+    nb = int(np.ceil(1.0 / bin_width - 1e-9))
+    ev, od, cum = np.zeros(len(t)), np.zeros(len(t)), np.zeros(nb)
+    spec, ipr = np.zeros((R, N)), np.zeros((R, N))
+    sw = np.zeros(R, dtype=np.int32)
+    rc = lib().ipeps_ed_run(ctypes.byref(p), _dptr(f), _dptr(t), _dptr(ev), _dptr(od), _dptr(cum),
+                            _dptr(spec), _dptr(ipr), sw.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                            stream)
+    _check(rc)
+    return dict(n_even=ev, n_odd=od, cum_ipr=cum, spectra=spec, ipr=ipr, sweeps=sw)

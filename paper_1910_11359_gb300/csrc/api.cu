@@ -369,7 +369,8 @@ static int capture_converge(Ctx& c, double tol_eff, bool use_tol) {
   if (!rc) rc = ctm_spectra(c, tol_eff, 0);
   if (!rc) {
     conv_test_kernel<<<1, 128, 0, c.st>>>(c.w.frozen, c.B, c.loopctl, use_tol ? 1 : 0, hs);
-    rc = cuda_fail(cudaGetLastError(), "conv test launch", __FILE__, __LINE__);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) rc = cuda_fail(e, "conv test launch", __FILE__, __LINE__);
   }
   if (!rc) rc = gb.loop_end();
   if (!rc) rc = gb.end(&exec);

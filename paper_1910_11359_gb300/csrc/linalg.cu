@@ -34,6 +34,8 @@ __global__ void __launch_bounds__(GT * GT) zgemm_kernel(GemmDesc g) {
   __shared__ cplx Bs[GT][GT + 1];
   const int tx = threadIdx.x % GT, ty = threadIdx.x / GT;
   const int m0 = blockIdx.y * GT, n0 = blockIdx.x * GT;
+  // a warp holds rows 2w and 2w + 1 of the tile (ty = threadIdx.x / 16)
+  const bool row_live = m0 + (ty & ~1) < g.M;
   cplx acc = cmk(0.0, 0.0);
   for (int k0 = 0; k0 < g.K; k0 += GT) {
     {  // A tile As[mm][kk]; for transposed storage let consecutive threads walk the stored row
@@ -49,8 +51,16 @@ __global__ void __launch_bounds__(GT * GT) zgemm_kernel(GemmDesc g) {
       Bs[kk][nn] = (gk < g.K && gn < g.N) ? load_op(B, g.ldb, g.opB, gk, gn) : cmk(0.0, 0.0);
     }
     __syncthreads();
+    // FP64 issue costs the same per warp-instruction whatever the active lanes, so a warp whose two
+    // rows both lie beyond M skips the products, and the last chunk stops at K
+    if (row_live) {
+      if (k0 + GT <= g.K) {
 #pragma unroll
-    for (int kk = 0; kk < GT; ++kk) cfma(acc, As[ty][kk], Bs[kk][tx]);
+        for (int kk = 0; kk < GT; ++kk) cfma(acc, As[ty][kk], Bs[kk][tx]);
+      } else {
+        for (int kk = 0; kk < g.K - k0; ++kk) cfma(acc, As[ty][kk], Bs[kk][tx]);
+      }
+    }
     __syncthreads();
   }
   const int gm = m0 + ty, gn = n0 + tx;
@@ -309,7 +319,8 @@ __global__ void __launch_bounds__(JTHREADS) jacobi_kernel(JacobiArgs args) {
       __syncthreads();
       if (tid == 0) nrot_total += nrot_round;
       if (flags[npairs + 1]) break;
-      const int rows = ra + rw;
+      // the accumulated right vectors (colW) are rotated only when V is wanted
+      const int rows = d.V ? ra + rw : ra;
       for (int idx = tid; idx < npairs * rows; idx += JTHREADS) {
         const int p = idx / rows, i = idx - p * rows;
         if (!flags[p]) continue;

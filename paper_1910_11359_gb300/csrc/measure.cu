@@ -4,8 +4,11 @@
 //
 // Every reduced density matrix is assembled from "left halves": in rotated frame f, at logical
 // position q, with the open (ket x bra) site tensor,
-//   Lh[e3r, c1r, s, s', kR] = C1 T1 T4 C4 T3 (around q) x ao[s, s', kU, kL, kD, kR]
-// where e3r / c1r are the right ends of T3 / T1 and kR the open right leg.
+//   Lh[e3r, c1r, s, s', kR] = C1 T1 T4 C4 T3 (around q) x A[s, uU, uL, uD, uR] conj(A)[s', bU, bL, bD, bR]
+// where e3r / c1r are the right ends of T3 / T1, each double leg k = (u, b) pairs a ket and a bra
+// index, and kR = (uR, bR) is the open right leg.  The ket and bra layers are contracted one after
+// the other (cost 8 chi^2 d D^7 + 8 chi^2 d^2 D^5 per left half) rather than as the open double
+// layer (8 chi^2 d^2 D^8, and d^2 D^8 numbers to hold).
 //   rho1(q)          = Lh_f0(q) . (C2 T2 C3)(q)                          (A at (0,0), B at (1,0))
 //   rho_h(p -> p+x)  = Lh_f0(p) . Lh_f2(p+x)                              (the right half is a left
 //   rho_v(p -> p+y)  = Lh_f1(rot p) . Lh_f3(rot^3 (p+y))                   half rotated by 180 deg)
@@ -20,29 +23,25 @@
 
 namespace ipeps {
 
-// open double layer, rotated and reshaped for the last contraction:
-// aoP[(i0 i1 i2), (s s' i3)] = rot^f(ao)[s, s', i0, i1, i2, i3], ao = A (x) conj(A) per leg
-__global__ void open_layer_kernel(const cplx* A, int d, int D, int B, int site_f_count, int f_of0,
-                                  cplx* out, int f) {
-  const int D2 = D * D, D4 = D2 * D2;
-  const long long rows = (long long)D2 * D2 * D2, cols = (long long)d * d * D2;
-  const long long per = rows * cols;
+// single layer, rotated and reshaped for the ket and bra contractions:
+// Ak[(a0 a1 a2), (s a3)] = rot^f(A)[s, a0, a1, a2, a3] (legs u, l, d, r of the rotated frame) and
+// Akc = conj(Ak); leg j of the unrotated tensor carries the rotated frame's index a_{(j + f) mod 4}
+__global__ void ket_layer_kernel(const cplx* A, int d, int D, int B, cplx* Ak, cplx* Akc, int f) {
+  const int D3 = D * D * D, D4 = D3 * D, cols = d * D;
+  const long long per = (long long)D3 * cols;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < (long long)B * per;
        idx += (long long)gridDim.x * blockDim.x) {
     const int b = (int)(idx / per);
-    const long long r = (idx % per) / cols, cc = idx % cols;
+    const int r = (int)((idx % per) / cols), cc = (int)(idx % cols);
     int p[4];
-    p[0] = (int)(r / (D2 * D2)); p[1] = (int)((r / D2) % D2); p[2] = (int)(r % D2);
-    const int s = (int)(cc / (d * D2)), sp = (int)((cc / D2) % d);
-    p[3] = (int)(cc % D2);
-    int ket = 0, bra = 0;
-    for (int j = 0; j < 4; ++j) {
-      const int q = p[(j + f) & 3];       // leg j of the unrotated tensor
-      ket = ket * D + q / D;
-      bra = bra * D + q % D;
-    }
-    const cplx* Ab = A + (size_t)b * d * D4;
-    out[idx] = cmulc(Ab[(size_t)sp * D4 + bra], Ab[(size_t)s * D4 + ket]);
+    p[0] = r / (D * D); p[1] = (r / D) % D; p[2] = r % D;
+    const int s = cc / D;
+    p[3] = cc % D;
+    int q = 0;
+    for (int j = 0; j < 4; ++j) q = q * D + p[(j + f) & 3];
+    const cplx v = A[(size_t)b * d * D4 + (size_t)s * D4 + q];
+    Ak[idx] = v;
+    Akc[idx] = cconj(v);
   }
 }
 
@@ -186,9 +185,10 @@ size_t measure_bytes(int B, int d, int D, int chi) {
 
 // jobs per pass: as many of the 8 B left-half jobs as fit their intermediates in kMeasurePassBytes
 // (at least one)
-int measure_group(int B, int D, int chi) {
-  const long long D2 = (long long)D * D, T = (long long)chi * D2 * chi;
-  const size_t per_job = sizeof(cplx) * (size_t)(2 * T + T * D2 + 2 * T * D2 * D2);
+int measure_group(int B, int d, int D, int chi) {
+  const long long D2 = (long long)D * D, T = (long long)chi * D2 * chi, chi2 = (long long)chi * chi;
+  const size_t per_job = sizeof(cplx) * (size_t)(2 * T + T * D2 + 2 * T * D2 * D2 + chi2 * d * D2 * D2 +
+                                                 chi2 * d * d * D2);
   const long long fit = (long long)(kMeasurePassBytes / per_job);
   return (int)std::max(1LL, std::min(fit, 8LL * B));
 }
@@ -196,13 +196,16 @@ int measure_group(int B, int D, int chi) {
 void measure_carve(Arena& a, MeasureWork& w, int B, int d, int D, int chi) {
   const long long D2 = (long long)D * D;
   const long long T = chi * D2 * chi;
-  const long long G = w.group = measure_group(B, D, chi);
+  const long long G = w.group = measure_group(B, d, D, chi), chi2 = (long long)chi * chi;
   w.tl = a.take<cplx>((size_t)G * T);
   w.W1 = a.take<cplx>((size_t)G * T * D2);
   w.bl = a.take<cplx>((size_t)G * T);
   w.W2 = a.take<cplx>((size_t)G * T * D2 * D2);
   w.W2p = a.take<cplx>((size_t)G * T * D2 * D2);
-  w.ao = a.take<cplx>((size_t)8 * B * d * d * D2 * D2 * D2 * D2);
+  w.X = a.take<cplx>((size_t)G * chi2 * d * D2 * D2);
+  w.Y = a.take<cplx>((size_t)G * chi2 * d * d * D2);
+  w.ak = a.take<cplx>((size_t)8 * B * d * D2 * D2);
+  w.akc = a.take<cplx>((size_t)8 * B * d * D2 * D2);
   w.Lh = a.take<cplx>((size_t)8 * B * chi * chi * d * d * D2);
   w.RCt = a.take<cplx>((size_t)2 * B * T);
   w.RC = a.take<cplx>((size_t)2 * B * T);
@@ -228,7 +231,7 @@ void measure_build(Ctx& c, MeasureWork& w, PtrPool& pool, MeasureOff& o) {
         w1A.push_back(Tp(3 + f, pp, b));
         blA.push_back(Tp(2 + f, pp, b));
         blB.push_back(Cp(3 + f, pp, b));
-        aoB.push_back(w.ao + (size_t)job * c.d * c.d * D2 * D2 * D2 * D2);
+        aoB.push_back(w.ak + (size_t)job * c.d * D2 * D2);
       }
   o.tlA = pool.add(tlA); o.tlB = pool.add(tlB); o.w1A = pool.add(w1A);
   o.blA = pool.add(blA); o.blB = pool.add(blB); o.aoB = pool.add(aoB);
@@ -268,13 +271,15 @@ int measure_run(Ctx& c, MeasureWork& w, const MeasurePlan& m, double* host_out) 
   const long long T = (long long)chi * D2 * chi;
   cudaStream_t st = c.st;
   int rc;
-  const long long aoper = (long long)d * d * D2 * D2 * D2 * D2;
+  const int D = c.D, D3 = D * D * D, dD = d * D;
+  const long long akper = (long long)D3 * dD, chi2 = (long long)chi * chi;
   for (int f = 0; f < 4; ++f)
     for (int l = 0; l < 2; ++l) {
       const cplx* A = l == 0 ? c.Aph : c.Bph;
-      IPEPS_LAUNCH(K_OPEN_LAYER, 0, st,
-                   open_layer_kernel<<<152 * 4, 256, 0, st>>>(A, d, c.D, B, 0, 0,
-                                                              w.ao + (size_t)(f * 2 + l) * B * aoper, f));
+      const size_t off = (size_t)(f * 2 + l) * B * akper;
+      const int blocks = (int)std::min<long long>((B * akper + 255) / 256, 152 * 4);
+      IPEPS_LAUNCH(K_KET_LAYER, 0, st,
+                   ket_layer_kernel<<<blocks, 256, 0, st>>>(A, d, D, B, w.ak + off, w.akc + off, f));
       IPEPS_CUDA_TRY(cudaGetLastError());
     }
   // left halves, in passes of w.group jobs (job = (f * 2 + l) * B + b)
@@ -297,14 +302,30 @@ int measure_run(Ctx& c, MeasureWork& w, const MeasurePlan& m, double* host_out) 
     g.C = w.W2; g.sC = T * D2 * D2; g.ldc = (long long)D2 * D2 * chi;
     if ((rc = zgemm_f64(g, st))) return rc;
     {
-      const int dims[5] = {chi, D2, D2, D2, chi}, perm[5] = {0, 4, 3, 2, 1};
-      if ((rc = permute_c128(w.W2, w.W2p, 5, dims, perm, G, T * D2 * D2, T * D2 * D2, st))) return rc;
+      // W2 [e3r][uD bD][uL bL][uU bU][c1r] -> W2p [e3r][c1r][bU bL bD][uU uL uD]
+      const int dims[8] = {chi, D, D, D, D, D, D, chi}, perm[8] = {0, 7, 6, 4, 2, 5, 3, 1};
+      if ((rc = permute_c128(w.W2, w.W2p, 8, dims, perm, G, T * D2 * D2, T * D2 * D2, st))) return rc;
     }
-    g = gdm(chi * chi, d * d * D2, D2 * D2 * D2, G);     // Lh = W2p aoP -> [e3r][c1r][s][s'][kR]
-    g.A = w.W2p; g.sA = T * D2 * D2; g.lda = (long long)D2 * D2 * D2;
-    g.Bptr = m.aoB + j0; g.ldb = (long long)d * d * D2;
-    g.C = w.Lh + (size_t)j0 * Lper; g.sC = Lper; g.ldc = (long long)d * d * D2;
+    // ket layer: X[(e3r c1r bU bL bD), (s uR)] = W2p . Ak
+    g = gdm(chi * chi * D3, dD, D3, G);
+    g.A = w.W2p; g.sA = T * D2 * D2; g.lda = D3;
+    g.Bptr = m.aoB + j0; g.ldb = dD;
+    g.C = w.X; g.sC = chi2 * D3 * dD; g.ldc = dD;
     if ((rc = zgemm_f64(g, st))) return rc;
+    // bra layer, per job and (e3r c1r): Y[(s uR), (s' bR)] = X^T conj(Ak)
+    for (int jj = 0; jj < G; ++jj) {
+      g = gdm(dD, dD, D3, chi * chi);
+      g.opA = OP_T; g.A = w.X + (size_t)jj * chi2 * D3 * dD; g.sA = (long long)D3 * dD; g.lda = dD;
+      g.B = w.akc + (size_t)(j0 + jj) * akper; g.sB = 0; g.ldb = dD;
+      g.C = w.Y + (size_t)jj * chi2 * dD * dD; g.sC = (long long)dD * dD; g.ldc = dD;
+      if ((rc = zgemm_f64(g, st))) return rc;
+    }
+    {
+      // Y [p][s][uR][s'][bR] -> Lh [p][s][s'][uR bR]
+      const int dims[5] = {chi * chi, d, D, d, D}, perm[5] = {0, 1, 3, 2, 4};
+      if ((rc = permute_c128(w.Y, w.Lh + (size_t)j0 * Lper, 5, dims, perm, G, chi2 * dD * dD, Lper, st)))
+        return rc;
+    }
   }
   GemmDesc g;
   // right column C2 T2 C3 at (0,0) and (1,0)

@@ -7,16 +7,17 @@ namespace ipeps {
 struct Ctx;
 
 // The eight left halves per instance are 8 B independent jobs (frame, site, instance); their
-// large intermediates (tl, W1, bl, W2, W2p) are held for `group` jobs at a time and the jobs run in
-// passes of that many, so the readout workspace stays bounded (kMeasurePassBytes) however large
-// D, chi and B are.  ao, Lh and everything after them hold all 8 B jobs.
+// large intermediates (tl, W1, bl, W2, W2p, X, Y) are held for `group` jobs at a time and the jobs
+// run in passes of that many, so the readout workspace stays bounded (kMeasurePassBytes) however
+// large D, chi and B are.  The single layers ak, akc, the left halves Lh and everything after them
+// hold all 8 B jobs.
 struct MeasureWork {
-  cplx *tl, *W1, *bl, *W2, *W2p, *ao, *Lh, *RCt, *RC, *rho1, *rho2;
+  cplx *tl, *W1, *bl, *W2, *W2p, *X, *Y, *ak, *akc, *Lh, *RCt, *RC, *rho1, *rho2;
   double* obs;
   int group;                // jobs per pass
 };
 constexpr size_t kMeasurePassBytes = size_t(4) << 30;
-int measure_group(int B, int D, int chi);
+int measure_group(int B, int d, int D, int chi);
 struct MeasureOff { size_t tlA, tlB, w1A, blA, blB, aoB, rcA, rcB, rcC, r1, r2; };
 struct MeasurePlan {
   const cplx* const* tlA; const cplx* const* tlB; const cplx* const* w1A;

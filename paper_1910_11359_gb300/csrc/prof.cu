@@ -13,8 +13,8 @@ namespace {
 const char* kNames[K_NCLASS] = {"zgemm_f64", "permute", "jacobi_svd", "su_absorb", "su_theta",
                                 "su_truncate", "su_rebuild", "gate", "phys_tensors", "double_layer",
                                 "env_init", "proj_prep", "normalize_store", "spectra_delta",
-                                "open_layer", "rho1", "rho2", "observables", "init_state", "bond_op",
-                                "tc_gemm_bf16", "tc_split_prep", "orth_cqr"};
+                                "ket_layer", "rho1", "rho2", "observables", "init_state", "bond_op",
+                                "tc_gemm_bf16", "tc_split_prep", "orth_cqr", "ed_elementwise"};
 std::atomic<unsigned long long> g_launches{0};
 std::mutex g_mu;
 std::atomic<bool> g_on{false};

@@ -8,8 +8,8 @@ namespace ipeps {
 
 enum KernelClass : int {
   K_ZGEMM = 0, K_PERMUTE, K_JACOBI, K_SU_ABSORB, K_SU_THETA, K_SU_TRUNCATE, K_SU_REBUILD, K_GATE,
-  K_PHYS, K_DLAYER, K_ENV_INIT, K_PROJ_PREP, K_NORM_STORE, K_SPECTRA, K_OPEN_LAYER, K_RHO1, K_RHO2,
-  K_OBS, K_INIT_STATE, K_BONDOP, K_TC_GEMM, K_TC_PREP, K_ORTH, K_NCLASS
+  K_PHYS, K_DLAYER, K_ENV_INIT, K_PROJ_PREP, K_NORM_STORE, K_SPECTRA, K_KET_LAYER, K_RHO1, K_RHO2,
+  K_OBS, K_INIT_STATE, K_BONDOP, K_TC_GEMM, K_TC_PREP, K_ORTH, K_ED, K_NCLASS
 };
 
 const char* kernel_class_name(int k);

@@ -12,6 +12,13 @@ request does not hold back short ones queued on the same worker.
 
 The engine is pluggable: LibraryEngine drives libipeps; the tests use a host-only engine.
 Every request's results are those of the same request run alone: each has its own handle.
+
+A run may be given a deadline (seconds after the start): admission stops there, the workers stop
+after the readout interval they are in, and requests not finished by then are returned in
+`unfinished` with the intervals they completed (a bounded window over a stream whose requests
+would take hours, e.g. D = 6 at chi = 108).  A worker still inside a long library call at the
+deadline is given `grace` seconds; after that run() returns without it (its request is listed as
+unfinished) and the caller should end the process rather than wait for it.
 """
 import threading
 import time
@@ -86,34 +93,50 @@ class Server:
         self.peak_used = 0
         self.queues = [[] for _ in range(workers)]       # per worker: active (request, state)
         self.done = []
+        self.unfinished = []
         self.errors = []
         self.t0 = None
+        self.deadline = None
+        self.grace = 5.0
 
     def _now(self):
         return time.perf_counter() - self.t0
 
-    def run(self, requests):
-        """Serve `requests` (their arrival times relative to the start); returns them finished."""
+    def _expired(self):
+        return self.deadline is not None and self._now() >= self.deadline
+
+    def run(self, requests, deadline=None):
+        """Serve `requests` (their arrival times relative to the start); returns them finished.
+        With a deadline, returns the requests finished by then (the others are in
+        self.unfinished)."""
         pending = sorted(requests, key=lambda r: (r.arrival, r.rid))
         for r in pending:
             if self.engine.footprint(r) > self.budget:
                 raise ValueError("request %d needs more memory than the whole budget" % r.rid)
+        self.deadline = deadline
         self.t0 = time.perf_counter()
         stop = threading.Event()
-        threads = [threading.Thread(target=self._worker, args=(w, stop)) for w in range(self.nworkers)]
+        threads = [threading.Thread(target=self._worker, args=(w, stop), daemon=True)
+                   for w in range(self.nworkers)]
         for t in threads:
             t.start()
         try:
             self._admit_loop(pending)
             with self.lock:
-                while len(self.done) < len(requests) and not self.errors:
+                while len(self.done) < len(requests) and not self.errors and not self._expired():
                     self.lock.wait(0.05)
         finally:
             stop.set()
             with self.lock:
                 self.lock.notify_all()
             for t in threads:
-                t.join()
+                t.join(None if deadline is None else self.grace)
+            with self.lock:
+                # requests of workers still busy past the grace period
+                for w in range(self.nworkers):
+                    for r, state, need in self.queues[w]:
+                        if r not in self.unfinished:
+                            self.unfinished.append(r)
         if self.errors:
             raise self.errors[0]
         return sorted(self.done, key=lambda r: r.rid)
@@ -123,6 +146,8 @@ class Server:
         for r in pending:
             need = self.engine.footprint(r)
             while not self.errors:
+                if self._expired():
+                    return
                 wait = r.arrival - self._now()
                 if wait > 0:
                     time.sleep(min(wait, 0.05))
@@ -154,10 +179,13 @@ class Server:
             with self.lock:
                 while not self.queues[w] and not stop.is_set():
                     self.lock.wait(0.05)
-                if stop.is_set() and not self.queues[w]:
+                if stop.is_set() and (not self.queues[w] or self._expired()):
+                    self._drop_unfinished(w)
                     return
                 batch = list(self.queues[w])
             for item in batch:
+                if self._expired():
+                    break
                 r, state, need = item
                 if state is None:
                     state, obs = self.engine.start(r, stream)
@@ -173,6 +201,16 @@ class Server:
                         r.finished = self._now()
                         self.done.append(r)
                         self.lock.notify_all()
+
+
+    def _drop_unfinished(self, w):
+        """(lock held) after the deadline: release the worker's unfinished requests."""
+        for r, state, need in self.queues[w]:
+            if state is not None:
+                self.engine.finish(r, state)
+            self.free += need
+            self.unfinished.append(r)
+        self.queues[w] = []
 
 
 def percentile(values, q):

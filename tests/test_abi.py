@@ -112,3 +112,32 @@ def test_noalloc_svd_rejects_blocks_beyond_shared_memory(lib):
                                       ctypes.c_double(1e-14), 10, vp(None), vp(None))
     assert rc == 8
     assert b"shared memory" in lib.ipeps_last_error(vp(None))
+
+
+def test_ed_rejects_before_any_device_work():
+    """The ED entry point validates on the host: a 40 x 40 lattice is beyond the device eigensolver
+    (EUNSUPPORTED), bad sizes are EINVAL, non-finite fields ENAN; ed_bytes sizes a 20 x 20 run."""
+    import ctypes
+    import numpy as np
+    import paper_1910_11359_gb300 as pkg
+    from paper_1910_11359_gb300._lib import EdParams
+    assert 400 <= pkg.ed_max_sites() < 1600
+    out = np.zeros(4)
+    sw = np.zeros(2, dtype=np.int32)
+    dp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    ip = sw.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    f = np.zeros(1600)
+    t = np.zeros(1)
+    p = EdParams(Lx=40, Ly=40, R=1, J=1.0, T=1, bin_width=0.05)
+    assert pkg.lib().ipeps_ed_run(ctypes.byref(p), dp(f), dp(t), dp(out), dp(out), dp(out), None, None, ip,
+                                  None) == 8
+    p = EdParams(Lx=4, Ly=4, R=0, J=1.0, T=1, bin_width=0.05)
+    assert pkg.lib().ipeps_ed_run(ctypes.byref(p), dp(f), dp(t), dp(out), dp(out), dp(out), None, None, ip,
+                                  None) == 1
+    f[3] = np.nan
+    p = EdParams(Lx=4, Ly=4, R=1, J=1.0, T=1, bin_width=0.05)
+    assert pkg.lib().ipeps_ed_run(ctypes.byref(p), dp(f), dp(t), dp(out), dp(out), dp(out), None, None, ip,
+                                  None) == 4
+    b = ctypes.c_size_t()
+    p = EdParams(Lx=20, Ly=20, R=100, J=1.0, T=51, bin_width=0.05)
+    assert pkg.lib().ipeps_ed_bytes(ctypes.byref(p), ctypes.byref(b)) == 0 and b.value > 10 ** 8

@@ -99,3 +99,20 @@ def test_percentile_and_request_stream():
     gaps = np.diff([0.0] + [r.arrival for r in rs])
     assert abs(np.mean(gaps) - 0.25) < 0.05
     assert all(r.D * r.D <= r.chi <= 3 * r.D * r.D for r in rs)
+
+
+def test_deadline_returns_finished_and_unfinished():
+    """With a deadline the server stops admitting, stops after the current intervals, returns the
+    requests finished by then and lists the rest (with the intervals they completed) as
+    unfinished; every admitted request's memory is returned."""
+    reqs = poisson_requests(40, rate=100.0, seed=7, d_choices=(2, 3, 4), t_max_choices=(1.0, 8.0),
+                            precision=0)
+    eng = FakeEngine(unit=0.01)
+    srv = Server(eng, budget_bytes=10 ** 6, workers=2)
+    out = srv.run(reqs, deadline=0.5)
+    assert out and srv.unfinished
+    assert len(out) + len(srv.unfinished) <= len(reqs)
+    assert all(len(r.readouts) == r.n_intervals + 1 for r in out)
+    assert all(len(r.readouts) <= r.n_intervals for r in srv.unfinished)
+    assert srv.free == srv.budget
+    assert eng.active == 0
