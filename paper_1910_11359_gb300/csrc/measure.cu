@@ -96,20 +96,26 @@ __global__ void rho2_kernel(const cplx* const* L1, const cplx* const* L2, int ch
   }
 }
 
+// z / w for complex w != 0
+__device__ __forceinline__ cplx cdiv(cplx z, cplx w) {
+  const double n = w.x * w.x + w.y * w.y;
+  return cmk((z.x * w.x + z.y * w.y) / n, (z.y * w.x - z.x * w.y) / n);
+}
+
 // Renyi entropies S_1, S_1/2, S_2 of the physical one-site RDM of A: the auxiliary level traced out
-// of rho_A (s = n * d_A + a), normalised; its two eigenvalues in closed form (2 x 2 Hermitian).
+// of rho_A (s = n * d_A + a) and the result divided by its (complex) trace; its two eigenvalues in
+// closed form (2 x 2 Hermitian).
 __device__ void renyi_phys(const cplx* r, int d, int dA, double* S1, double* Sh, double* S2) {
-  double a = 0.0, c = 0.0;
-  cplx off = cmk(0.0, 0.0);
+  cplx a = cmk(0.0, 0.0), c = cmk(0.0, 0.0), off = cmk(0.0, 0.0);
   for (int x = 0; x < dA; ++x) {
-    a += r[(size_t)x * d + x].x;                           // n = 0
-    c += r[(size_t)(dA + x) * d + dA + x].x;               // n = 1
-    off = cadd(off, r[(size_t)x * d + dA + x]);            // <n=0| rho |n=1>
+    a = cadd(a, r[(size_t)x * d + x]);                            // n = 0
+    c = cadd(c, r[(size_t)(dA + x) * d + dA + x]);                // n = 1
+    off = cadd(off, r[(size_t)x * d + dA + x]);                   // <n=0| rho |n=1>
   }
-  const double tr = a + c;
-  a /= tr; c /= tr;
-  const double ox = off.x / tr, oy = off.y / tr;
-  const double mid = 0.5 * (a + c), rad = sqrt(0.25 * (a - c) * (a - c) + ox * ox + oy * oy);
+  const cplx tr = cadd(a, c);
+  const double an = cdiv(a, tr).x, cn = cdiv(c, tr).x;
+  const cplx o = cdiv(off, tr);
+  const double mid = 0.5 * (an + cn), rad = sqrt(0.25 * (an - cn) * (an - cn) + o.x * o.x + o.y * o.y);
   double p[2] = {fmax(mid + rad, 0.0), fmax(mid - rad, 0.0)};
   double s1 = 0.0, sq = 0.0, p2 = 0.0;
   for (int i = 0; i < 2; ++i) {
@@ -123,48 +129,55 @@ __device__ void renyi_phys(const cplx* r, int d, int dA, double* S1, double* Sh,
 }
 
 // Observables per instance from rho1 (A, B) and the four bond RDMs:
-// out[b] = {nA, nB, I, tauzA, tauzB, energy, purityA, tr_rhoA, S1_A, S1/2_A, S2_A}
+// out[b] = {nA, nB, I, tauzA, tauzB, energy, purityA, |tr rho_A|, S1_A, S1/2_A, S2_A}.
+// Every RDM is divided by its own complex trace: the environment fixes the network's value only up
+// to a complex factor, which a ratio of real parts would not remove from the quadratic quantities
+// (purity, Renyi entropies).
 __global__ void observables_kernel(const cplx* rho1, const cplx* rho2, const cplx* bondop,
                                    const double* h, int B, int d, int dA, double* out) {
   const int b = blockIdx.x;
   if (threadIdx.x != 0) return;
   const int d2 = d * d;
-  double n[2], tz[2], tn[2], tr[2];
+  double n[2], tz[2], tn[2];
+  cplx tr[2];
   for (int site = 0; site < 2; ++site) {
     const cplx* r = rho1 + (size_t)(site * B + b) * d2;
-    double trc = 0.0, nn = 0.0, tt = 0.0, tnn = 0.0;
+    cplx trc = cmk(0.0, 0.0), nn = cmk(0.0, 0.0), tt = cmk(0.0, 0.0), tnn = cmk(0.0, 0.0);
     for (int s = 0; s < d; ++s) {
-      const double p = r[s * d + s].x;
+      const cplx p = r[s * d + s];
       const int occ = s / dA;
       const double lev = dA > 1 ? 1.0 - 2.0 * (s % dA) / (dA - 1) : 0.0;
-      trc += p; nn += occ * p; tt += lev * p; tnn += lev * occ * p;
+      trc = cadd(trc, p);
+      nn = cadd(nn, cscale(p, occ));
+      tt = cadd(tt, cscale(p, lev));
+      tnn = cadd(tnn, cscale(p, lev * occ));
     }
-    tr[site] = trc; n[site] = nn / trc; tz[site] = tt / trc; tn[site] = tnn / trc;
+    tr[site] = trc;
+    n[site] = cdiv(nn, trc).x; tz[site] = cdiv(tt, trc).x; tn[site] = cdiv(tnn, trc).x;
   }
   double eb = 0.0;
   const cplx* H = bondop + (size_t)b * d2 * d2;
   for (int k = 0; k < 4; ++k) {
     const cplx* r = rho2 + (size_t)(k * B + b) * d2 * d2;
-    cplx num = cmk(0.0, 0.0);
-    double den = 0.0;
+    cplx num = cmk(0.0, 0.0), den = cmk(0.0, 0.0);
     for (int s = 0; s < d; ++s)
       for (int t = 0; t < d; ++t)
         for (int v = 0; v < d; ++v)
           for (int w = 0; w < d; ++w)
             cfma(num, H[(size_t)(t * d + w) * d2 + s * d + v], r[((s * d + t) * d + v) * d + w]);
     for (int s = 0; s < d; ++s)
-      for (int v = 0; v < d; ++v) den += r[((s * d + s) * d + v) * d + v].x;
-    eb += num.x / den;
+      for (int v = 0; v < d; ++v) den = cadd(den, r[((s * d + s) * d + v) * d + v]);
+    eb += cdiv(num, den).x;
   }
   const cplx* rA = rho1 + (size_t)b * d2;
-  double pur = 0.0;
+  cplx pur = cmk(0.0, 0.0);
   for (int s = 0; s < d; ++s)
-    for (int t = 0; t < d; ++t) pur += cmul(rA[s * d + t], rA[t * d + s]).x;
-  pur /= tr[0] * tr[0];
+    for (int t = 0; t < d; ++t) pur = cadd(pur, cmul(rA[s * d + t], rA[t * d + s]));
+  pur = cdiv(pur, cmul(tr[0], tr[0]));
   double* o = out + (size_t)b * kObsPerInstance;
   o[0] = n[0]; o[1] = n[1]; o[2] = n[0] - n[1]; o[3] = tz[0]; o[4] = tz[1];
   o[5] = 0.5 * (eb + h[b] * (tn[0] + tn[1]));
-  o[6] = pur; o[7] = tr[0];
+  o[6] = pur.x; o[7] = sqrt(tr[0].x * tr[0].x + tr[0].y * tr[0].y);
   renyi_phys(rA, d, dA, &o[8], &o[9], &o[10]);
 }
 
