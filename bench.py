@@ -388,7 +388,7 @@ def native_main(args):
     tfile = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tfile):
         tj = json.load(open(tfile))
-        if tj.get("kernel") == name and tj.get("workload") == WORKLOAD and tj.get("source_sha") == _kernel_sha():
+        if tj.get("kernel") == name and tj.get("workload") == WORKLOAD and tj.get("source_sha") == _kernel_sha(name):
             traffic = tj.get("dram_bytes_per_launch")
     shares = {k: round(v[0] / prof_ms, 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])
               if v[0] > 0}
@@ -451,14 +451,20 @@ def native_main(args):
     return 0
 
 
-def _kernel_sha():
-    """Hash of the CUDA sources, to tell whether a stored ncu traffic figure still describes them."""
+# source files that define each kernel class the roofline may name (the kernel and what it includes)
+KERNEL_SOURCES = {"jacobi_svd": ("linalg.cu", "linalg.cuh", "common.cuh", "prof.cuh"),
+                  "zgemm_f64": ("linalg.cu", "linalg.cuh", "common.cuh", "prof.cuh")}
+
+
+def _kernel_sha(kernel="jacobi_svd"):
+    """Hash of the sources of one kernel class (all CUDA sources for a class not listed), to tell
+    whether a stored ncu traffic figure still describes that kernel."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1910_11359_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    files = KERNEL_SOURCES.get(kernel) or tuple(f for f in os.listdir(csrc) if f.endswith((".cu", ".cuh")))
+    for f in sorted(files):
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 

@@ -29,6 +29,7 @@
 #include "model.cuh"
 #include "orth.cuh"
 #include "prof.cuh"
+#include "reduce.cuh"
 #include "tc_gemm.cuh"
 
 namespace ipeps {
@@ -459,16 +460,9 @@ __global__ void normalize_store_kernel(const cplx* C1n, const cplx* T4n, const c
   const long long n = kind == 1 ? nT : nC;
   const cplx* src = (kind == 0 ? C1n : kind == 1 ? T4n : C4n) + (size_t)q * n;
   cplx* dst = (kind == 0 ? sC1 : kind == 1 ? sT4 : sC4)[q];
-  __shared__ double red[256];
   double m = 0.0;
   for (long long i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, cabs2(src[i]));
-  red[threadIdx.x] = m;
-  __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]);
-    __syncthreads();
-  }
-  const double mx = sqrt(red[0]);
+  const double mx = sqrt(block_max<256>(m));
   if (!isfinite(mx) && threadIdx.x == 0) atomicOr(err, (unsigned)DEV_NONFINITE);
   const double f = mx > 0.0 ? 1.0 / mx : 0.0;
   for (long long i = threadIdx.x; i < n; i += blockDim.x) dst[i] = cscale(src[i], f);

@@ -20,6 +20,7 @@
 #include "ctx.cuh"
 #include "measure.cuh"
 #include "prof.cuh"
+#include "reduce.cuh"
 
 namespace ipeps {
 
@@ -51,21 +52,14 @@ __global__ void rho1_kernel(const cplx* Lh, const cplx* RC, int chi, int D2, int
   const long long per = (long long)chi * chi * d * d * D2;
   const cplx* L = Lh + (size_t)q * per;
   const cplx* R = RC + (size_t)q * chi * D2 * chi;
-  __shared__ cplx red[256];
   for (int ss = 0; ss < d * d; ++ss) {
     cplx acc = cmk(0.0, 0.0);
     for (long long t = threadIdx.x; t < (long long)chi * chi * D2; t += blockDim.x) {
       const int a = (int)(t / (chi * D2)), bb = (int)((t / D2) % chi), k = (int)(t % D2);
       cfma(acc, L[(((size_t)a * chi + bb) * d * d + ss) * D2 + k], R[((size_t)bb * D2 + k) * chi + a]);
     }
-    red[threadIdx.x] = acc;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-      if (threadIdx.x < o) red[threadIdx.x] = cadd(red[threadIdx.x], red[threadIdx.x + o]);
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) rho[(size_t)q * d * d + ss] = red[0];
-    __syncthreads();
+    const cplx sum = block_sum<256>(acc);
+    if (threadIdx.x == 0) rho[(size_t)q * d * d + ss] = sum;
   }
 }
 
@@ -77,22 +71,16 @@ __global__ void rho2_kernel(const cplx* const* L1, const cplx* const* L2, int ch
   const int ss = e / d2, vv = e % d2;
   const cplx* X = L1[job];
   const cplx* Yp = L2[job];
-  __shared__ cplx red[256];
   cplx acc = cmk(0.0, 0.0);
   for (long long t = threadIdx.x; t < (long long)chi * chi * D2; t += blockDim.x) {
     const int a = (int)(t / (chi * D2)), bb = (int)((t / D2) % chi), k = (int)(t % D2);
     cfma(acc, X[(((size_t)a * chi + bb) * d2 + ss) * D2 + k], Yp[(((size_t)bb * chi + a) * d2 + vv) * D2 + k]);
   }
-  red[threadIdx.x] = acc;
-  __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] = cadd(red[threadIdx.x], red[threadIdx.x + o]);
-    __syncthreads();
-  }
+  const cplx sum = block_sum<256>(acc);
   if (threadIdx.x == 0) {
     // rho index [s][s'][v][v'] from ss = s * d + s', vv = v * d + v'
     const int s = ss / d, sp = ss % d, v = vv / d, vp = vv % d;
-    rho[(size_t)job * d2 * d2 + ((s * d + sp) * d + v) * d + vp] = red[0];
+    rho[(size_t)job * d2 * d2 + ((s * d + sp) * d + v) * d + vp] = sum;
   }
 }
 
