@@ -699,7 +699,7 @@ def _serve_run(prec, args):
 
 
 def serve_main(args):
-    """Serving loop on the config-5 stream: seeded Poisson requests (mean 4 per second), D in 2..6,
+    """Serving loop on the request stream: seeded Poisson requests (mean 4 per second), D in 2..6,
     chi in [D^2, 3 D^2], h in [0.5, 16], V in {0, 0.5, 1}, t_max in {2, 4, 8}, readouts every 0.5,
     admitted by footprint under half of the free device memory and run on 4 worker streams, split
     precision; then the same stream on the FP64 path.  A D = 6, chi = 108 request alone runs for

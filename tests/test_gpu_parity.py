@@ -117,7 +117,7 @@ def _validity(GA, GB, lam, C, T, obs, chi, D, cut_rel=ctmrg.PROJ_CUT_REL, d_A=2)
     return e_read, 1e-10 + 1e-14 * kappa, ctmrg.spectra_delta(s1, s0), sens
 
 
-def oracle_from_env(GA, GB, lam, C, T, chi, cut_rel=ctmrg.PROJ_CUT_REL, d_A=2, tol=1e-12, max_sweeps=300):
+def oracle_from_env(GA, GB, lam, C, T, chi, cut_rel=ctmrg.PROJ_CUT_REL, d_A=2, tol=1e-11, max_sweeps=200):
     """The oracle's own CTMRG continued from the GPU's environment (with the GPU's tensors) until the
     corner spectra change by less than ``tol`` (no stall exit); returns (converged, one-site readout).
     A converged run that stays at the GPU's readout shows that the GPU's environment is an
@@ -257,7 +257,7 @@ def _compare_rows(out, g, keys, chi, D, cold=False):
         if u and not capped and e >= UNIQUE_TOL:
             # the oracle's probes are local: they do not see a second attracting fixed point that a
             # start from elsewhere (the GPU's path from the traced start, other rounding) can reach.
-            # Evidence of one: the oracle's own CTMRG, continued from the GPU's environment to 1e-12,
+            # Evidence of one: the oracle's own CTMRG, continued from the GPU's environment to 1e-11,
             # stays at the GPU's readout (within its convergence level) and is at least 1e-8 away from
             # the golden readout (far beyond the golden's own convergence error).  Such a row has two
             # correct readouts: reported, not compared.

@@ -1,5 +1,5 @@
 """The split-precision path (BF16x3 tensor-core contractions, FP64 projectors and readout) along the
-config-2 trajectory, against the FP64 oracle's golden trajectories.
+D = 3, chi = 18 quench trajectory (h = 1, 5, 10), against the FP64 oracle's golden trajectories.
 
 The bar of the split path is the imbalance (and the occupations) within 1e-4 of the FP64 result.
 It is applied to every readout whose result the oracle shows to be unique (the same rule as the
@@ -48,7 +48,7 @@ def test_split_quench_d3_tracks_oracle():
             e = max(abs(obs[b][k] - row["cold"][k]) for k in ("imbalance", "nA", "nB"))
             if uniq and e >= 1e-4:
                 # a second fixed point the oracle's local probes do not see: the oracle's own FP64
-                # CTMRG, continued from the split path's environment to 1e-12, stays within the split
+                # CTMRG, continued from the split path's environment to 1e-11, stays within the split
                 # bar of the split readout and away from the golden one by more than that bar (the
                 # same rule as the FP64 parity tests)
                 C, T = sim.get_env(b)
