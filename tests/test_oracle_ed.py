@@ -114,3 +114,16 @@ def test_cumulative_ipr_bins():
     assert len(c) == 20 and abs(c.sum() - 1.5) < 1e-15
     assert c[0] == 0.1 and c[19] == 0.5 and c[10] == 0.3 and c[5] == 0.2
     assert c[12] == 0.4          # eps = 2.5 / 4 = 0.625 -> interval 12
+
+
+def test_ed_fields_recipe():
+    """The seeded on-site fields: continuous ones uniform in [-h, h]; discrete ones only the levels
+    -h + 2 h k / (s - 1), all of them used, each with frequency near 1 / s; reproducible by seed."""
+    c = ed_fields(20, 50, 4.0, 0, seed=2)
+    assert c.shape == (50, 400) and c.min() >= -4.0 and c.max() <= 4.0
+    assert abs(c.mean()) < 0.05 and abs(c.var() - 16.0 / 3.0) < 0.1
+    d = ed_fields(20, 50, 10.0, 3, seed=2)
+    vals, counts = np.unique(d, return_counts=True)
+    assert np.allclose(vals, [-10.0, 0.0, 10.0])
+    assert np.all(np.abs(counts / d.size - 1.0 / 3.0) < 0.01)
+    assert np.array_equal(ed_fields(6, 3, 1.0, 0, seed=9), ed_fields(6, 3, 1.0, 0, seed=9))
