@@ -6,10 +6,11 @@ A plain 2 x 4 torus would double the bonds across its width-2 direction, which c
 O(t^2) coefficient of the imbalance; the tilted cluster keeps the infinite lattice's local
 structure up to loops that wrap the torus.
 
-The exact disorder average of the dilated model equals the uniform mean over all 2^8 auxiliary
-configurations tau in {+1, -1}^8 of the plain boson model with fields h tau_i (Sec. "Set up for
-iPEPS", Readout).  Each configuration is evolved from the CDW (4 particles on sublattice A) in the
-70-dimensional N = 4 sector by exact eigendecomposition.
+The exact disorder average of the dilated model equals the uniform mean over all d_A^8 auxiliary
+configurations of the plain boson model with fields h tau_i, tau_i in the d_A levels
+1 - 2 a / (d_A - 1) (+1, -1 for d_A = 2; +1, 0, -1 for d_A = 3) (Sec. "Set up for iPEPS", Readout).
+Each configuration is evolved from the CDW (4 particles on sublattice A) in the 70-dimensional
+N = 4 sector by exact eigendecomposition.
 """
 import itertools
 
@@ -37,7 +38,7 @@ def cluster():
     return sites, sorted(bonds), sub
 
 
-def imbalance(J, V, h, times):
+def imbalance(J, V, h, times, d_A=2):
     sites, bonds, sub = cluster()
     L = len(sites)
     basis = [c for c in itertools.combinations(range(L), L // 2)]
@@ -59,7 +60,8 @@ def imbalance(J, V, h, times):
     A = np.array([i for i in range(L) if sub[i] == 0])
     B = np.array([i for i in range(L) if sub[i] == 1])
     out = np.zeros(len(times))
-    for taus in itertools.product((1.0, -1.0), repeat=L):
+    levels = [1.0 - 2.0 * a / (d_A - 1) for a in range(d_A)]
+    for taus in itertools.product(levels, repeat=L):
         H = Hkin + np.diag(Hint + h * occ @ np.array(taus))
         w, W = np.linalg.eigh(H)
         c0 = W.T @ psi0
@@ -67,4 +69,4 @@ def imbalance(J, V, h, times):
             psi = W @ (np.exp(-1j * w * t) * c0)
             n = (np.abs(psi) ** 2) @ occ
             out[it] += n[A].mean() - n[B].mean()
-    return out / 2 ** L
+    return out / d_A ** L

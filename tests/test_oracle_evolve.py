@@ -6,7 +6,8 @@
 * J -> -J and h -> -h leave I(t) unchanged (pin P3); <tau^z> stays 0 and n_A + n_B stays 1 up to
   the truncation error (pin P5).
 * Short-time agreement with exact dynamics of the 8-site tilted cluster averaged over all 2^8
-  disorder configurations, with an O(t^4) finite-size gap (pin P9).
+  disorder configurations, with an O(t^4) finite-size gap (pin P9); the same at three disorder
+  levels (d_A = 3, all 3^8 configurations), with J = 0 exactness and the 1 - 8 t^2 law there too.
 * Cold and warm CTMRG starts give the same observables.
 """
 import numpy as np
@@ -102,3 +103,30 @@ def test_convergence_in_chi_and_d():
     c = evolve.run(dict(base, D=3, chi=9, t_max=0.1))
     assert abs(a[1]["imbalance"] - c[1]["imbalance"]) < 1e-4
     assert c[-1]["trunc_err_acc"] < a[1]["trunc_err_acc"]
+
+
+def test_three_levels_zero_hopping_and_short_time():
+    """d_A = 3 (fields h, 0, -h per site): J = 0 keeps the CDW (I = 1); the short-time law
+    I = 1 - 8 J^2 t^2 + O(t^4) holds whatever the levels."""
+    out = _run(J=0.0, d_A=3, t_max=0.2, dt=0.02, meas_every=0.1, order=1)
+    for o in out:
+        assert abs(o['imbalance'] - 1.0) < 1e-13
+    out = _run(d_A=3, dt=0.001, t_max=0.04, meas_every=0.01)
+    t = np.array([o['t'] for o in out[1:]])
+    y = 1 - np.array([o['imbalance'] for o in out[1:]])
+    coef, *_ = np.linalg.lstsq(np.stack([t ** 2, t ** 4], 1), y, rcond=None)
+    assert abs(coef[0] - 8.0) < 0.02, coef
+
+
+def test_three_levels_track_exact_dynamics_of_8_site_cluster():
+    """d_A = 3 against the 8-site cluster averaged over all 3^8 = 6561 disorder configurations:
+    the O(t^4) finite-size gap of the two-level pin (observed 5e-5 at t = 0.05, 7.7e-4 at 0.1)."""
+    times = [0.05, 0.1]
+    ex = ed.imbalance(1.0, 1.0, 5.0, times, d_A=3)
+    out = _run(D=2, chi=8, order=2, dt=0.01, t_max=0.1, meas_every=0.05, d_A=3)
+    diff = [abs(o['imbalance'] - e) for o, e in zip(out[1:], ex)]
+    assert diff[0] < 1e-4 and diff[1] < 1.5e-3
+    assert 8 < diff[1] / diff[0] < 24          # the gap grows like t^4
+    t = np.array([0.01, 0.02])
+    ex = ed.imbalance(1.0, 1.0, 5.0, t, d_A=3)
+    assert np.all(np.abs(ex - (1 - 8 * t * t)) < 60 * t ** 4)
