@@ -90,6 +90,8 @@ def test_null_handles_and_bad_sizes_fail_cleanly(lib):
         lambda: lib.ipeps_get_tensors(vp(None), vp(None), vp(None)),
         lambda: lib.ipeps_get_env(vp(None), 0, vp(None), vp(None)),
         lambda: lib.ipeps_set_env(vp(None), 0, vp(None), vp(None)),
+        lambda: lib.ipeps_set_graphs(vp(None), 1),
+        lambda: lib.ipeps_ed_bytes(vp(None), vp(None)),
         # m < n, and a batch beyond the allocation-free entry point's fixed scratch
         lambda: lib.ipeps_kernel_svd(3, 5, 1, vp(1), vp(None), vp(1), vp(None), ctypes.c_double(1e-14),
                                      10, vp(None), vp(None)),
