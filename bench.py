@@ -770,6 +770,8 @@ def ed_main(args):
     pkg.profile_enable(False)
     total = sum(v[0] for v in prof.values())
     reals = 2 * R * args.steps
+    dom_name, (dom_ms, dom_flops, dom_n) = max(prof.items(), key=lambda kv: kv[1][0])
+    dom_tf = dom_flops / (dom_ms * 1e-3) / 1e12 if dom_ms > 0 else 0.0
     # the oracle on 4 realisations of the continuous case, one thread (BLAS / LAPACK pinned to 1)
     code = ("import sys, time; sys.path.insert(0, %r); from inputs import ED, ed_fields; from oracle import ed; "
             "f = ed_fields(20, 100, 10.0, 0, seed=31)[:4]; t = time.perf_counter(); "
@@ -786,6 +788,10 @@ def ed_main(args):
                                  "per call)"},
             "kernel_time_share": {k: round(v[0] / total, 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])
                                   if v[0] > 0},
+            "roofline": {"bound": "alu", "kernel": dom_name, "achieved": dom_tf, "peak": FP64_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": dom_tf / FP64_PEAK_TFLOPS, "traffic": None,
+                         "launches": dom_n, "avg_launch_us": 1e3 * dom_ms / max(dom_n, 1),
+                         "timing": "CUDA events per launch in a separate profiled call (both disorder kinds)"},
             "jacobi_sweeps_mean": float(np.mean(out["sweeps"])),
             "gpu_launches": int(launches),
             "cpu_baseline": {"value": 4 / osec, "unit": "realisations/s", "cores": 1, "kind": "oracle",
